@@ -1,0 +1,169 @@
+/*
+ * sawave: subspace-accelerated sigma-transformed Poisson solve on one GB300.
+ *
+ * C ABI of the library libsawave.so.  The method is that of
+ * "Subspace Acceleration for Efficient Nonlinear Water Wave Simulation"
+ * (Sorensen, Guido, Engsig-Karup, Kressner): every stage of a low-storage
+ * Runge-Kutta step of the free-surface Navier-Stokes model solves
+ *     A(tau) x(tau) = b(tau)                                   (Eq. 1, Eq. 19)
+ * with the mixed-stage sigma-transformed operator of Eq. (16)-(18), by GMRES
+ * left-preconditioned with one fixed ILU factorisation (Sec. 3), started from
+ * the exponentially weighted subspace guess of Algorithms 2 and 4.
+ *
+ * Conventions for every entry point:
+ *   - the return value is a status code (SW_OK or a negative SW_ERR_*);
+ *   - pointers named d_* are device pointers (cudaMalloc or torch memory on the
+ *     current device), pointers named h_* are host pointers; the caller owns
+ *     every buffer it passes and the library never frees or keeps them;
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Work is enqueued on that stream; calls that return
+ *     statistics synchronise it;
+ *   - the library owns everything it allocates (ILU factors, Krylov basis,
+ *     subspace sketch, scratch) and releases it in sw_destroy_problem;
+ *   - there is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns SW_ERR_CUDA.
+ *
+ * Grid and node numbering.  The sigma grid has nx * ny columns (ny = 1 in 2-D),
+ * periodic in x (and y), and nz sigma levels sigma_j = j/(nz-1), j = 0..nz-1,
+ * plus one ghost level j = -1 below the bed (Sec. 5.1).  A field on the grid
+ * is an array of m = nx*ny*(nz+1) doubles, node (ix, iy, j) at index
+ * ((j+1)*ny + iy)*nx + ix.  Surface fields (eta, h) hold nx*ny doubles,
+ * index iy*nx + ix.  Requirements: nz >= 7; nx and ny (when ny > 1) are
+ * multiples of 4 and at least 8.
+ */
+#ifndef SAWAVE_H
+#define SAWAVE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SW_OK 0
+#define SW_ERR_BAD_ARG (-1)          /* invalid argument or unsupported size */
+#define SW_ERR_CUDA (-2)             /* a CUDA call failed (message via sw_last_error) */
+#define SW_ERR_NOT_CONVERGED (-3)    /* iteration cap reached; x holds the last iterate */
+#define SW_ERR_SINGULAR_PRECOND (-4) /* zero pivot in the ILU factorisation */
+#define SW_ERR_NAN (-5)              /* non-finite residual during a solve */
+
+#define SW_GUESS_COLD 0      /* x0 = 0 */
+#define SW_GUESS_PREVIOUS 1  /* x0 = previous solution (the paper's baseline, Sec. 5.1) */
+#define SW_GUESS_EWMA 2      /* Algorithm 4 with V = Y (Algorithm 2) */
+
+#define SW_PRECISION_FP64 0  /* every step in FP64 */
+#define SW_PRECISION_MIXED 1 /* FP32 inner GMRES cycles, FP64 outer residual */
+
+typedef struct sw_problem sw_problem;
+
+typedef struct {
+    int nx, ny, nz;  /* columns in x and y, sigma levels (ghost level not counted) */
+    double lx, ly;   /* periodic domain lengths (ly ignored when ny == 1) */
+} sw_grid;
+
+typedef struct {
+    int restart;        /* GMRES restart length m (Sec. 3; 20 for the workloads here) */
+    int max_restarts;   /* restart cycles allowed after the first one */
+    double tol;         /* stop when ||M^-1(b - A x)|| <= tol ||M^-1 b|| */
+    int guess;          /* SW_GUESS_* */
+    int k;              /* EWMA sketch width k (Algorithm 4), 1..16 */
+    double decay;       /* forgetting rate r of Algorithm 4, applied once per solve, in (0, 1] */
+    int n_init_solves;  /* solves run with the previous-solution guess before EWMA starts (N_init, Sec. 5.1) */
+    int precision;      /* SW_PRECISION_* */
+    uint64_t seed;      /* seed of the Gaussian sketch vectors omega */
+} sw_params;
+
+typedef struct {
+    int iterations;        /* Arnoldi steps of the last solve (all cycles) */
+    int restarts;          /* cycles after the first in the last solve */
+    int converged;         /* 1 when the last solve met the tolerance */
+    int status;            /* status of the last solve */
+    double res0;           /* ||M^-1(b - A x0)|| / ||M^-1 b|| of the last solve */
+    double res_final;      /* same at the returned solution */
+    double true_res;       /* ||b - A x|| / ||b|| at the returned solution */
+    double guess_res;      /* ||b - A x0|| / ||b|| */
+    long long n_solves;    /* solves since creation */
+    long long total_iterations;
+} sw_stats;
+
+typedef struct {
+    double g;    /* gravity */
+    double rho;  /* density */
+    double dt;   /* time step Delta tau */
+} sw_physics;
+
+/* Build a problem on the current CUDA device.  h_depth: host array of nx*ny
+ * still-water depths h > 0.  Computes the ILU(0) factors of the operator at
+ * still water (eta = 0) on the host in FP64 (Sec. 3 and Sec. 5), in the
+ * four-colour column ordering, and uploads them.  On success *out owns all
+ * device memory of the problem.  Errors: SW_ERR_BAD_ARG (sizes, parameters),
+ * SW_ERR_SINGULAR_PRECOND, SW_ERR_CUDA. */
+int sw_create_problem(const sw_grid *grid, const sw_params *params, const double *h_depth, sw_problem **out);
+
+/* Release everything the problem owns.  NULL is accepted. */
+int sw_destroy_problem(sw_problem *p);
+
+/* Number of unknowns m = nx*ny*(nz+1). */
+int sw_problem_size(const sw_problem *p, long long *m);
+
+/* Solve A(eta_prev, eta_cur) x = b (Eq. 16-18; Algorithm 2 with the guess
+ * selected in the parameters; for EWMA the sketch is updated with the new
+ * solution, Algorithm 4).  d_eta_prev, d_eta_cur: nx*ny surfaces at stages
+ * i-1 and i; d_b, d_x: m doubles.  Enqueued on `stream`; returns SW_OK once
+ * enqueued.  The outcome (status, iterations, residuals) is read with
+ * sw_get_stats. */
+int sw_solve_poisson(sw_problem *p, const double *d_eta_prev, const double *d_eta_cur,
+                     const double *d_b, double *d_x, void *stream);
+
+/* The same solve with host buffers: copies eta_prev, eta_cur and b to the
+ * device, solves, copies x back and synchronises `stream`.  Returns the
+ * solve status. */
+int sw_solve_poisson_host(sw_problem *p, const double *h_eta_prev, const double *h_eta_cur,
+                          const double *h_b, double *h_x, void *stream);
+
+/* Statistics of the last solve (synchronises the stream of that solve). */
+int sw_get_stats(sw_problem *p, sw_stats *out);
+
+/* y = A(eta_prev, eta_cur) x, matrix-free (Eq. 16-18).  Device pointers. */
+int sw_apply_operator(sw_problem *p, const double *d_eta_prev, const double *d_eta_cur,
+                      const double *d_x, double *d_y, void *stream);
+
+/* out = U^-1 L^-1 v with the fixed ILU(0) factors (Sec. 3).  Device pointers,
+ * out must not alias v. */
+int sw_apply_preconditioner(sw_problem *p, const double *d_v, double *d_out, void *stream);
+
+/* EWMA guess alone (Algorithm 2 with V = Y): x0 = Y z*, z* = argmin ||A Y z - b||,
+ * with A = A(eta_prev, eta_cur) and the problem's current sketch Y. */
+int sw_subspace_guess(sw_problem *p, const double *d_eta_prev, const double *d_eta_cur,
+                      const double *d_b, double *d_x0, void *stream);
+
+/* Sketch access: Y is m x k, column c at offset c*m.  Device pointers. */
+int sw_get_sketch(sw_problem *p, double *d_Y, void *stream);
+int sw_set_sketch(sw_problem *p, const double *d_Y, long long n_solves, void *stream);
+
+/* The Gaussian sketch vector omega of a given solve (host): SplitMix64
+ * outputs 2(s k + c) + 1 and 2(s k + c) + 2 through Box-Muller, c = 0..k-1. */
+int sw_draw_omega(uint64_t seed, long long solve_index, int k, double *h_omega);
+
+/* ---- stage driver: Algorithm 1 with LSERK45 (Sec. 3 and Sec. 5) ---- */
+
+/* Physical constants and time step for the stage driver. */
+int sw_set_physics(sw_problem *p, const sw_physics *phys);
+/* Load the state: u, w (and v in 3-D, else NULL) on the m nodes, eta on the
+ * surface; the Runge-Kutta registers are zeroed and the stage counter reset.
+ * Device pointers, copied. */
+int sw_set_state(sw_problem *p, const double *d_u, const double *d_v, const double *d_w,
+                 const double *d_eta, void *stream);
+/* Copy the state out (any of the pointers may be NULL). */
+int sw_get_state(sw_problem *p, double *d_u, double *d_v, double *d_w, double *d_eta,
+                 double *d_p, void *stream);
+/* One stage i (cycling 1..5) of Algorithm 1: K_eta and eta^(i), the right-hand
+ * side of Eq. (16)-(17), the Poisson solve, K_u and u^(i). */
+int sw_advance_stage(sw_problem *p, void *stream);
+
+/* Last error message of the calling thread (static storage). */
+const char *sw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

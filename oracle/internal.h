@@ -1,0 +1,45 @@
+/* Internal state of the oracle problem.  TEST INFRASTRUCTURE ONLY. */
+#ifndef SAWAVE_ORACLE_INTERNAL_H
+#define SAWAVE_ORACLE_INTERNAL_H
+#include "oracle.h"
+
+struct or_problem {
+    or_grid g;
+    or_params p;
+    int ncol;            /* nx * ny */
+    int m;               /* ncol * (nz + 1) */
+    int box;             /* structural pattern includes the sigma-cross terms */
+    double dx, dy;
+    double wx1[OR_W], wx2[OR_W], wy1[OR_W], wy2[OR_W];  /* centred periodic weights */
+    double *ws1, *ws2;   /* (nz+1) x 7 sigma weights, row j+1 */
+    int *win;            /* (nz+1) first window level, row j+1 */
+    double *h, *hx, *hy, *hxx, *hyy;  /* bathymetry and its surface-grid derivatives */
+    or_csr A;            /* last assembled operator */
+    or_csr A0;           /* still-water operator on the preconditioner pattern */
+    or_csr LU;           /* ILU(0) factors in the permuted ordering (L unit lower + U) */
+    int *order, *rank;   /* order[new] = old, rank[old] = new */
+    int *diag;           /* position of the diagonal in each row of LU */
+    double *Y;           /* EWMA sketch, k columns of length m, column-major */
+    double *x_prev;      /* last solution */
+    long n_solves;
+    double *work;        /* scratch */
+};
+
+/* Column-geometry of one free surface, Sec. 2.1 (13b-13d). */
+typedef struct {
+    double *d, *dx, *dy, *dxx, *dyy;
+} or_colgeom;
+
+void or_colgeom_alloc(const or_problem *P, or_colgeom *G);
+void or_colgeom_free(or_colgeom *G);
+void or_colgeom_eval(const or_problem *P, const double *eta, or_colgeom *G);
+/* Periodic surface-grid derivatives D_chi, D_chichi, D_gamma, D_gammagamma (Sec. 3). */
+void or_surface_derivs(const or_problem *P, const double *f, double *fx, double *fy,
+                       double *fxx, double *fyy);
+/* 3-D field derivatives at all nodes. */
+void or_field_dx(const or_problem *P, const double *f, double *out);
+void or_field_dy(const or_problem *P, const double *f, double *out);
+void or_field_dsigma(const or_problem *P, const double *f, double *out);
+void or_csr_free(or_csr *A);
+double or_sigma(const or_problem *P, int j);
+#endif

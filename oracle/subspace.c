@@ -1,0 +1,147 @@
+/*
+ * Subspace acceleration of the oracle.  TEST INFRASTRUCTURE ONLY.
+ *
+ * Algorithm 2: pick a basis V of a subspace of span of past solutions, solve
+ *   z* = argmin_z || A V z - b ||_2   (by a QR factorisation, Sec. 4),
+ * and start the iterative solver from x0 = V z*.
+ * Algorithm 4 (EWMA): V = Y with Y = sum over past solutions of
+ *   r^(age) x omega^T, updated after every solve as Y <- r Y + x omega^T
+ *   (the rank-1 form printed below Algorithm 4).  omega ~ N(0, I_k).
+ * The age is counted in solves (one decay factor r per solve); see the
+ * reading recorded with the decay parameter.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include "internal.h"
+
+/* SplitMix64 (Steele, Lea & Flood 2014): i-th output (i >= 1) of the stream with
+ * the given seed is the finaliser applied to seed + i * golden-gamma. */
+uint64_t or_splitmix64(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + i * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* omega_c for solve s: Box-Muller on outputs 2(s k + c) + 1 and 2(s k + c) + 2. */
+void or_draw_omega(uint64_t seed, long solve_index, int k, double *omega)
+{
+    const double two53 = 1.0 / 9007199254740992.0;
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int c = 0; c < k; ++c) {
+        uint64_t i1 = 2 * ((uint64_t)solve_index * (uint64_t)k + (uint64_t)c) + 1;
+        double u1 = ((double)(or_splitmix64(seed, i1) >> 11) + 1.0) * two53;   /* (0, 1] */
+        double u2 = (double)(or_splitmix64(seed, i1 + 1) >> 11) * two53;       /* [0, 1) */
+        double rr = sqrt(-2.0 * log(u1));
+        double th = two_pi * u2;
+        omega[c] = rr * cos(th);
+    }
+}
+
+/* Householder QR of W (m x k, column-major), then z = R^-1 (Q^T b)[0:k].
+ * Columns whose |R_jj| falls below 1e-12 |R_00| are treated as dependent
+ * and get z_j = 0.  Returns the numerical rank. */
+int or_lstsq_qr(int m, int k, const double *W, const double *b, double *z)
+{
+    double *R = malloc((size_t)m * k * sizeof(double));
+    double *qb = malloc(m * sizeof(double));
+    double *v = malloc(m * sizeof(double));
+    double *diag = malloc(k * sizeof(double));
+    memcpy(R, W, (size_t)m * k * sizeof(double));
+    memcpy(qb, b, m * sizeof(double));
+    for (int j = 0; j < k && j < m; ++j) {
+        double *cj = R + (size_t)j * m;
+        double nx = 0;
+        for (int i = j; i < m; ++i) nx += cj[i] * cj[i];
+        nx = sqrt(nx);
+        if (nx == 0.0) { diag[j] = 0.0; continue; }
+        double alpha = cj[j] > 0 ? -nx : nx;
+        for (int i = j; i < m; ++i) v[i] = cj[i];
+        v[j] -= alpha;
+        double vn = 0;
+        for (int i = j; i < m; ++i) vn += v[i] * v[i];
+        diag[j] = alpha;
+        if (vn == 0.0) continue;
+        /* H = I - 2 v v^T / (v^T v) on the remaining columns and on b */
+        for (int l = j; l < k; ++l) {
+            double *cl = R + (size_t)l * m;
+            double s = 0;
+            for (int i = j; i < m; ++i) s += v[i] * cl[i];
+            s = 2.0 * s / vn;
+            for (int i = j; i < m; ++i) cl[i] -= s * v[i];
+        }
+        double s = 0;
+        for (int i = j; i < m; ++i) s += v[i] * qb[i];
+        s = 2.0 * s / vn;
+        for (int i = j; i < m; ++i) qb[i] -= s * v[i];
+    }
+    int rank = 0;
+    double r00 = k > 0 ? fabs(diag[0]) : 0.0;
+    for (int j = k - 1; j >= 0; --j) {
+        double rjj = R[(size_t)j * m + j];
+        if (!(fabs(rjj) > 1e-12 * r00) ) { z[j] = 0.0; continue; }
+        double s = qb[j];
+        for (int l = j + 1; l < k; ++l) s -= R[(size_t)l * m + j] * z[l];
+        z[j] = s / rjj;
+        rank++;
+    }
+    free(R); free(qb); free(v); free(diag);
+    return rank;
+}
+
+int or_ewma_guess(or_problem *P, const double *b, double *x0)
+{
+    int m = P->m, k = P->p.k;
+    double *W = malloc((size_t)m * k * sizeof(double));
+    double z[64];
+    for (int c = 0; c < k; ++c) or_matvec(P, P->Y + (size_t)c * m, W + (size_t)c * m);
+    int rank = or_lstsq_qr(m, k, W, b, z);
+    for (int i = 0; i < m; ++i) {
+        double s = 0;
+        for (int c = 0; c < k; ++c) s += P->Y[(size_t)c * m + i] * z[c];
+        x0[i] = s;
+    }
+    free(W);
+    return rank;
+}
+
+void or_ewma_update(or_problem *P, const double *x, long solve_index)
+{
+    int m = P->m, k = P->p.k;
+    double om[64];
+    or_draw_omega(P->p.seed, solve_index, k, om);
+    for (int c = 0; c < k; ++c) {
+        double *yc = P->Y + (size_t)c * m;
+        for (int i = 0; i < m; ++i) yc[i] = P->p.decay * yc[i] + x[i] * om[c];
+    }
+}
+
+void or_get_sketch(const or_problem *P, double *Y)
+{
+    memcpy(Y, P->Y, (size_t)P->m * P->p.k * sizeof(double));
+}
+
+void or_set_sketch(or_problem *P, const double *Y)
+{
+    memcpy(P->Y, Y, (size_t)P->m * P->p.k * sizeof(double));
+}
+
+int or_solve(or_problem *P, const double *eta_prev, const double *eta_cur, const double *b,
+             double *x_out, or_stats *st)
+{
+    int m = P->m;
+    or_assemble(P, eta_prev, eta_cur);
+    long s = P->n_solves;
+    int mode = P->p.guess;
+    if (mode == OR_GUESS_EWMA && (s < P->p.n_init_solves || P->p.k == 0)) mode = OR_GUESS_PREV;
+    if (mode == OR_GUESS_COLD) for (int i = 0; i < m; ++i) x_out[i] = 0.0;
+    else if (mode == OR_GUESS_PREV) memcpy(x_out, P->x_prev, m * sizeof(double));
+    else or_ewma_guess(P, b, x_out);
+    int status = or_gmres(P, b, x_out, st);
+    memcpy(P->x_prev, x_out, m * sizeof(double));
+    if (P->p.guess == OR_GUESS_EWMA && P->p.k > 0) or_ewma_update(P, x_out, s);
+    P->n_solves++;
+    return status;
+}

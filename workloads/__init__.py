@@ -1,0 +1,156 @@
+"""Seeded synthetic inputs for the sigma-transformed Poisson solve.
+
+This module only makes input data: bathymetry h, initial free surface eta and
+initial velocities (u, v, w) from linear (Airy) wave theory, plus the grid sizes
+and time step of each workload.  It contains none of the solver's arithmetic
+and is shared by the tests, the benchmark and the oracle checks.
+
+Stand-ins: the paper initialises stream-function waves from Fenton's Fourier
+method and runs the Beji-Battjes flume (Sec. 5); neither Fenton's solutions
+nor the flume data are available here, so the workloads below use sums of
+linear waves of the same wavenumber, depth and steepness class instead.
+"""
+import math
+
+import numpy as np
+
+G = 9.81
+RHO = 1000.0
+
+
+def sigma_levels(nz):
+    """sigma_j = j/(nz-1) for j = -1 (ghost) .. nz-1."""
+    return np.arange(-1, nz) / (nz - 1.0)
+
+
+def node_z(h, eta, nz):
+    """Physical z of every node, shape (nz+1, ncol): z = sigma d - h."""
+    s = sigma_levels(nz)[:, None]
+    d = (h + eta)[None, :]
+    return s * d - h[None, :]
+
+
+def dispersion_omega(k, h):
+    return np.sqrt(G * k * np.tanh(k * h))
+
+
+def airy_fields(x, y, h, nz, comps):
+    """Linear superposition of progressive waves.
+
+    comps: list of (kx, ky, amplitude, phase).  Returns eta (ncol,), u, v, w
+    (each (nz+1)*ncol, x fastest then y then sigma, ghost level first).
+    """
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    X = X.ravel(); Y = Y.ravel()
+    eta = np.zeros(X.size)
+    for kx, ky, a, ph in comps:
+        eta += a * np.cos(kx * X + ky * Y + ph)
+    Z = node_z(h, eta, nz)
+    u = np.zeros_like(Z); v = np.zeros_like(Z); w = np.zeros_like(Z)
+    for kx, ky, a, ph in comps:
+        k = math.hypot(kx, ky)
+        om = dispersion_omega(k, h)[None, :]
+        th = (kx * X + ky * Y + ph)[None, :]
+        hz = (Z + h[None, :])
+        ch = np.cosh(k * hz) / np.sinh(k * h)[None, :]
+        sh = np.sinh(k * hz) / np.sinh(k * h)[None, :]
+        u += a * om * (kx / k) * ch * np.cos(th)
+        v += a * om * (ky / k) * ch * np.cos(th)
+        w += a * om * sh * np.sin(th)
+    return eta, u.ravel(), v.ravel(), w.ravel()
+
+
+def courant_dt(dx, lmax, hmax, cr=0.5):
+    """dt with Courant number cr for the phase speed of the longest periodic wave."""
+    k = 2 * math.pi / lmax
+    c = math.sqrt(G / k * math.tanh(k * hmax))
+    return cr * dx / c
+
+
+def _wl(nx, ny, nz, lx, ly, h, comps, steps, name, **extra):
+    x = np.arange(nx) * (lx / nx)
+    y = np.arange(ny) * (ly / ny) if ny > 1 else np.zeros(1)
+    eta, u, v, w = airy_fields(x, y, h, nz, comps)
+    dx = lx / nx
+    if ny > 1:
+        dx = min(dx, ly / ny)
+    dt = courant_dt(dx, max(lx, ly if ny > 1 else 0.0), float(h.max()))
+    d = dict(name=name, nx=nx, ny=ny, nz=nz, lx=lx, ly=(ly if ny > 1 else 0.0), h=h, eta=eta, u=u,
+             v=(v if ny > 1 else None), w=w, dt=dt, steps=steps, g=G, rho=RHO, m=nx * ny * (nz + 1))
+    d.update(extra)
+    return d
+
+
+def airy_2d(nx=64, nz=9, kh=1.0, a_over_h=0.01, depth=1.0, steps=50):
+    """Linear Airy wave in a periodic 2-D slice, flat bed (the 64 x 9 workload)."""
+    k = kh / depth
+    lx = 2 * math.pi / k
+    h = np.full(nx, depth)
+    return _wl(nx, 1, nz, lx, 0.0, h, [(k, 0.0, a_over_h * depth, 0.0)], steps, "airy2d_%dx%d" % (nx, nz))
+
+
+def stokes_like_2d(nx=512, nz=17, kh=2.0, a1_over_h=0.08, depth=1.0, n_harm=4, ratio=0.3, seed=2511,
+                   steps=1000):
+    """Steep periodic wave: first n_harm harmonics a_n = a1 ratio^(n-1), seeded phases."""
+    rng = np.random.default_rng(seed)
+    k = kh / depth
+    lx = 2 * math.pi / k
+    phases = rng.uniform(0, 2 * math.pi, n_harm)
+    comps = [(n * k, 0.0, a1_over_h * depth * ratio ** (n - 1), phases[n - 1]) for n in range(1, n_harm + 1)]
+    h = np.full(nx, depth)
+    return _wl(nx, 1, nz, lx, 0.0, h, comps, steps, "stokes2d_%dx%d" % (nx, nz))
+
+
+def periodic_bar_2d(nx=256, nz=9, kh=1.5, a_over_h=0.02, depth=1.0, bar_frac=0.25, bar_height=0.5, seed=7,
+                    steps=50):
+    """Periodic 2-D slice over a trapezoidal bar (variable depth, box pattern)."""
+    rng = np.random.default_rng(seed)
+    k = kh / depth
+    lx = 2 * math.pi / k
+    x = np.arange(nx) * (lx / nx)
+    c0 = rng.uniform(0.3, 0.7) * lx
+    top = bar_frac * lx * 0.3
+    ramp = bar_frac * lx * 0.35
+    dist = np.abs(x - c0)
+    prof = np.clip((top + ramp - dist) / ramp, 0.0, 1.0)
+    h = depth * (1.0 - bar_height * prof)
+    phase = rng.uniform(0, 2 * math.pi)
+    return _wl(nx, 1, nz, lx, 0.0, h, [(k, 0.0, a_over_h * depth, phase)], steps, "bar2d_%dx%d" % (nx, nz))
+
+
+def bumpy_3d(nx=256, ny=256, nz=17, depth=1.0, n_bumps=8, n_comp=16, amp_sum=0.03, seed=4, steps=500):
+    """3-D periodic field over seeded Gaussian bumps (depth 1 + 0.2 * bumps)."""
+    rng = np.random.default_rng(seed)
+    L = 2 * math.pi
+    x = np.arange(nx) * (L / nx)
+    y = np.arange(ny) * (L / ny)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    bump = np.zeros_like(X)
+    for _ in range(n_bumps):
+        cx, cy = rng.uniform(0, L, 2)
+        s = rng.uniform(0.3, 0.8)
+        dxp = np.minimum(np.abs(X - cx), L - np.abs(X - cx))
+        dyp = np.minimum(np.abs(Y - cy), L - np.abs(Y - cy))
+        bump += np.exp(-(dxp ** 2 + dyp ** 2) / (2 * s * s))
+    h = depth + 0.2 * depth * bump / bump.max()
+    comps = []
+    amps = rng.uniform(0.5, 1.0, n_comp)
+    amps *= amp_sum * depth / amps.sum()
+    for q in range(n_comp):
+        while True:
+            kx, ky = rng.integers(-4, 5, 2)
+            if 1.0 <= math.hypot(kx, ky) <= 4.0:
+                break
+        comps.append((float(kx), float(ky), float(amps[q]), float(rng.uniform(0, 2 * math.pi))))
+    return _wl(nx, ny, nz, L, L, h.ravel(), comps, steps, "bumpy3d_%dx%dx%d" % (nx, ny, nz))
+
+
+def state_arrays(wl):
+    """Fresh RK state for a workload: copies of u, v, w, eta and zero registers."""
+    st = dict(u=wl["u"].copy(), v=None if wl["v"] is None else wl["v"].copy(), w=wl["w"].copy(),
+              eta=wl["eta"].copy())
+    st["Ku"] = np.zeros_like(st["u"])
+    st["Kv"] = None if st["v"] is None else np.zeros_like(st["v"])
+    st["Kw"] = np.zeros_like(st["w"])
+    st["Keta"] = np.zeros_like(st["eta"])
+    return st
