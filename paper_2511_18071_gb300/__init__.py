@@ -1,0 +1,243 @@
+"""sawave: subspace-accelerated sigma-transformed Poisson solve on GB300.
+
+Thin ctypes binding of libsawave.so (C ABI in include/sawave.h).  Every
+function here only marshals arguments: torch CUDA tensors become device
+pointers, the current torch stream becomes the cudaStream_t.  All arithmetic
+runs in the library's CUDA kernels; there is no CPU fallback, and importing
+this package fails loudly when the library has not been built.
+"""
+import ctypes as C
+import os
+
+from . import build as _build
+
+__all__ = ["Grid", "Params", "Stats", "Physics", "Problem", "create_problem", "destroy_problem", "problem_size",
+           "solve_poisson", "solve_poisson_host", "get_stats", "apply_operator", "apply_preconditioner",
+           "subspace_guess", "get_sketch", "set_sketch", "draw_omega", "set_physics", "set_state", "get_state",
+           "advance_stage", "library_path", "SawaveError", "GUESS", "PRECISION"]
+
+SW_OK = 0
+STATUS = {0: "OK", -1: "BAD_ARG", -2: "CUDA_ERR", -3: "NOT_CONVERGED", -4: "SINGULAR_PRECOND", -5: "NAN"}
+GUESS = {"cold": 0, "previous": 1, "ewma": 2}
+PRECISION = {"fp64": 0, "mixed": 1}
+
+
+class SawaveError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double), ("ly", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("restart", C.c_int), ("max_restarts", C.c_int), ("tol", C.c_double), ("guess", C.c_int),
+                ("k", C.c_int), ("decay", C.c_double), ("n_init_solves", C.c_int), ("precision", C.c_int),
+                ("seed", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int), ("status", C.c_int),
+                ("res0", C.c_double), ("res_final", C.c_double), ("true_res", C.c_double),
+                ("guess_res", C.c_double), ("n_solves", C.c_longlong), ("total_iterations", C.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Physics(C.Structure):
+    _fields_ = [("g", C.c_double), ("rho", C.c_double), ("dt", C.c_double)]
+
+
+def library_path():
+    return _build.LIB
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libsawave.so; raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("libsawave.so is not built (run __graft_entry__.build() or "
+                              "python -m paper_2511_18071_gb300.build); there is no CPU fallback")
+        L = C.CDLL(path)
+        vp, ip = C.c_void_p, C.c_int
+        L.sw_create_problem.argtypes = [C.POINTER(Grid), C.POINTER(Params), vp, C.POINTER(vp)]
+        L.sw_destroy_problem.argtypes = [vp]
+        L.sw_problem_size.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.sw_solve_poisson.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sw_solve_poisson_host.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sw_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.sw_apply_operator.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sw_apply_preconditioner.argtypes = [vp, vp, vp, vp]
+        L.sw_subspace_guess.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sw_get_sketch.argtypes = [vp, vp, vp]
+        L.sw_set_sketch.argtypes = [vp, vp, C.c_longlong, vp]
+        L.sw_draw_omega.argtypes = [C.c_uint64, C.c_longlong, ip, vp]
+        L.sw_set_physics.argtypes = [vp, C.POINTER(Physics)]
+        L.sw_set_state.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sw_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.sw_advance_stage.argtypes = [vp, vp]
+        L.sw_last_error.restype = C.c_char_p
+        for name in ["sw_create_problem", "sw_destroy_problem", "sw_problem_size", "sw_solve_poisson",
+                     "sw_solve_poisson_host", "sw_get_stats", "sw_apply_operator", "sw_apply_preconditioner",
+                     "sw_subspace_guess", "sw_get_sketch", "sw_set_sketch", "sw_draw_omega", "sw_set_physics",
+                     "sw_set_state", "sw_get_state", "sw_advance_stage"]:
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code, allow=()):
+    if code != SW_OK and code not in allow:
+        raise SawaveError(code, lib().sw_last_error().decode(errors="replace"))
+    return code
+
+
+def _dptr(t):
+    """Device pointer of a contiguous CUDA float64 tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    """Host pointer of a contiguous float64 numpy array or CPU tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous CPU float64 tensor")
+        return C.c_void_p(a.data_ptr())
+    import numpy as np
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a contiguous float64 array")
+    return C.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(stream)
+
+
+# ---- C-ABI mirrors (same names as include/sawave.h without the sw_ prefix) ----
+
+def create_problem(grid, params, h_depth):
+    import numpy as np
+    h = np.ascontiguousarray(h_depth, dtype=np.float64)
+    out = C.c_void_p()
+    _check(lib().sw_create_problem(C.byref(grid), C.byref(params), C.c_void_p(h.ctypes.data), C.byref(out)))
+    return out
+
+
+def destroy_problem(p):
+    return _check(lib().sw_destroy_problem(p))
+
+
+def problem_size(p):
+    m = C.c_longlong()
+    _check(lib().sw_problem_size(p, C.byref(m)))
+    return m.value
+
+
+def solve_poisson(p, eta_prev, eta_cur, b, x, stream=None):
+    return _check(lib().sw_solve_poisson(p, _dptr(eta_prev), _dptr(eta_cur), _dptr(b), _dptr(x), _stream(stream)))
+
+
+def solve_poisson_host(p, eta_prev, eta_cur, b, x, stream=None):
+    return _check(lib().sw_solve_poisson_host(p, _hptr(eta_prev), _hptr(eta_cur), _hptr(b), _hptr(x),
+                                              _stream(stream)), allow=(-3,))
+
+
+def get_stats(p):
+    st = Stats()
+    _check(lib().sw_get_stats(p, C.byref(st)))
+    return st.as_dict()
+
+
+def apply_operator(p, eta_prev, eta_cur, x, y, stream=None):
+    return _check(lib().sw_apply_operator(p, _dptr(eta_prev), _dptr(eta_cur), _dptr(x), _dptr(y), _stream(stream)))
+
+
+def apply_preconditioner(p, v, out, stream=None):
+    return _check(lib().sw_apply_preconditioner(p, _dptr(v), _dptr(out), _stream(stream)))
+
+
+def subspace_guess(p, eta_prev, eta_cur, b, x0, stream=None):
+    return _check(lib().sw_subspace_guess(p, _dptr(eta_prev), _dptr(eta_cur), _dptr(b), _dptr(x0), _stream(stream)))
+
+
+def get_sketch(p, Y, stream=None):
+    return _check(lib().sw_get_sketch(p, _dptr(Y), _stream(stream)))
+
+
+def set_sketch(p, Y, n_solves, stream=None):
+    return _check(lib().sw_set_sketch(p, _dptr(Y), int(n_solves), _stream(stream)))
+
+
+def draw_omega(seed, solve_index, k):
+    import numpy as np
+    out = np.zeros(k)
+    _check(lib().sw_draw_omega(seed, solve_index, k, C.c_void_p(out.ctypes.data)))
+    return out
+
+
+def set_physics(p, phys):
+    return _check(lib().sw_set_physics(p, C.byref(phys)))
+
+
+def set_state(p, u, v, w, eta, stream=None):
+    return _check(lib().sw_set_state(p, _dptr(u), _dptr(v), _dptr(w), _dptr(eta), _stream(stream)))
+
+
+def get_state(p, u=None, v=None, w=None, eta=None, pres=None, stream=None):
+    return _check(lib().sw_get_state(p, _dptr(u), _dptr(v), _dptr(w), _dptr(eta), _dptr(pres), _stream(stream)))
+
+
+def advance_stage(p, stream=None):
+    return _check(lib().sw_advance_stage(p, _stream(stream)))
+
+
+class Problem:
+    """Owning handle around sw_problem with torch-tensor conveniences."""
+
+    def __init__(self, nx, ny, nz, lx, ly, h, restart=20, max_restarts=50, tol=1e-8, guess="cold", k=10,
+                 decay=0.9, n_init_solves=30, precision="fp64", seed=2511):
+        self.grid = Grid(nx, ny, nz, lx, ly if ny > 1 else 0.0)
+        self.params = Params(restart, max_restarts, tol, GUESS[guess], k, decay, n_init_solves,
+                             PRECISION[precision], seed)
+        self.handle = create_problem(self.grid, self.params, h)
+        self.m = problem_size(self.handle)
+        self.ncol = nx * ny
+        self.nx, self.ny, self.nz, self.k = nx, ny, nz, k
+
+    def close(self):
+        if getattr(self, "handle", None):
+            destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, eta_prev, eta_cur, b, x, stream=None):
+        return solve_poisson(self.handle, eta_prev, eta_cur, b, x, stream)
+
+    def stats(self):
+        return get_stats(self.handle)

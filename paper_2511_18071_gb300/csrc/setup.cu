@@ -1,0 +1,478 @@
+// Host-side set-up of a problem: finite-difference weights, the still-water
+// operator in slot form, its ILU(0) factorisation in the four-colour column
+// ordering, and the device allocations.
+//
+// Preconditioner (Sec. 3 and Sec. 5): one incomplete LU factorisation of the
+// operator built for the still-water state eta = 0, computed once and reused
+// for every stage.  Variant ILU(0): fill restricted to the sparsity pattern of
+// that operator.  Ordering: colour (ix + iy) mod 4 first, then the column, then
+// the level from the ghost level up; with nx, ny multiples of four, columns of
+// one colour never share a 7-point stencil, which lets the device sweep all
+// columns of a colour at once.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+
+#include "sw_internal.cuh"
+
+namespace sw {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return SW_ERR_CUDA;
+}
+
+// Derivative weights at z from the Lagrange basis polynomials through nodes
+// x[0..6]: the d-th derivative of l_i at z is d! times the coefficient of
+// (x - z)^d in prod_{q != i} (x - x_q) / prod_{q != i} (x_i - x_q).
+static void lagrange_weights(const long double *x, long double z, double *w1, double *w2) {
+    for (int i = 0; i < W; ++i) {
+        long double c[W] = {1.0L};  // coefficients in powers of t = x - z
+        int deg = 0;
+        long double den = 1.0L;
+        for (int q = 0; q < W; ++q) {
+            if (q == i) continue;
+            long double r = x[q] - z;  // factor (t - r)
+            for (int p = deg + 1; p >= 1; --p) c[p] = c[p - 1] - r * c[p];
+            c[0] = -r * c[0];
+            ++deg;
+            den *= (x[i] - x[q]);
+        }
+        w1[i] = (double)(c[1] / den);
+        w2[i] = (double)(2.0L * c[2] / den);
+    }
+}
+
+static int sigma_window(int nz, int j) {
+    int s = j - HALF;
+    if (s < -1) s = -1;
+    if (s > nz - W) s = nz - W;
+    return s;
+}
+
+namespace {
+
+struct Host {
+    int nx, ny, nz, P, ncol, layout, nslot, three_d;
+    long long m;
+    double dx, dy;
+    double wx1[W], wx2[W], wy1[W], wy2[W];
+    std::vector<double> ws1, ws2;   // P x W
+    std::vector<int> win;           // P
+    std::vector<double> h, hx, hy, hxx, hyy;
+
+    int colour(int ix, int iy) const { return (ix + iy) & 3; }
+    long long rank_of(int ix, int iy, int j) const {
+        int c = colour(ix, iy);
+        long long q = (long long)iy * (nx / 4) + (ix >> 2);
+        return ((long long)c * (ncol / 4) + q) * P + (j + 1);
+    }
+    void node_of_rank(long long r, int &ix, int &iy, int &j) const {
+        long long per = (long long)(ncol / 4) * P;
+        int c = (int)(r / per);
+        long long rem = r % per;
+        long long q = rem / P;
+        j = (int)(rem % P) - 1;
+        iy = (int)(q / (nx / 4));
+        ix = ((c - iy) & 3) + 4 * (int)(q % (nx / 4));
+    }
+    int wrapx(int i) const { i %= nx; return i < 0 ? i + nx : i; }
+    int wrapy(int i) const { i %= ny; return i < 0 ? i + ny : i; }
+
+    // neighbour of slot s for row (ix, iy, j)
+    void slot_nb(int s, int ix, int iy, int j, int &nx_, int &ny_, int &lev) const {
+        static const int off[6] = {-3, -2, -1, 1, 2, 3};
+        int ox = 0, oy = 0;
+        int w0 = win[j + 1];
+        switch (layout) {
+        case CROSS2D:
+            if (s < 6) { ox = off[s]; lev = j; } else { lev = w0 + (s - 6); }
+            break;
+        case BOX2D:
+            ox = s / 7 - 3; lev = w0 + s % 7;
+            break;
+        case CROSS3D:
+            if (s < 6) { ox = off[s]; lev = j; }
+            else if (s < 12) { oy = off[s - 6]; lev = j; }
+            else { lev = w0 + (s - 12); }
+            break;
+        default:
+            if (s < 49) { ox = s / 7 - 3; lev = w0 + s % 7; }
+            else { oy = off[(s - 49) / 7]; lev = w0 + (s - 49) % 7; }
+        }
+        nx_ = wrapx(ix + ox);
+        ny_ = ny > 1 ? wrapy(iy + oy) : 0;
+    }
+    // structural pattern of the still-water operator in this row
+    bool in_pattern(int s, int j) const {
+        if (j == nz - 1) return s == sigma_slot(layout, W - 1);
+        if (j == -1) {
+            int ss = sigma_slot(layout, 0);
+            if (s >= ss && s < ss + W) return true;
+            if (layout == CROSS2D || layout == CROSS3D) return false;
+            // box: horizontal entries at the bed level (window offset 1)
+            if (layout == BOX2D) return s % 7 == 1;
+            return (s < 49 ? s % 7 : (s - 49) % 7) == 1;
+        }
+        return true;
+    }
+    // slot of row (ix, iy, j) that refers to node (bx, by, lev), or -1
+    int find_slot(int ix, int iy, int j, int bx, int by, int lev) const {
+        int dxo = bx - ix, dyo = by - iy;
+        if (dxo > nx / 2) dxo -= nx;
+        if (dxo < -nx / 2) dxo += nx;
+        if (ny > 1) { if (dyo > ny / 2) dyo -= ny; if (dyo < -ny / 2) dyo += ny; }
+        int kk = lev - win[j + 1];
+        auto xoff = [](int o) { return o < 0 ? o + 3 : o + 2; };  // -3..-1,1..3 -> 0..5
+        switch (layout) {
+        case CROSS2D:
+            if (dxo == 0) return (kk >= 0 && kk < W) ? 6 + kk : -1;
+            if (lev == j && dxo >= -3 && dxo <= 3) return xoff(dxo);
+            return -1;
+        case BOX2D:
+            if (dxo >= -3 && dxo <= 3 && kk >= 0 && kk < W) return (dxo + 3) * 7 + kk;
+            return -1;
+        case CROSS3D:
+            if (dxo == 0 && dyo == 0) return (kk >= 0 && kk < W) ? 12 + kk : -1;
+            if (lev != j) return -1;
+            if (dyo == 0 && dxo >= -3 && dxo <= 3) return xoff(dxo);
+            if (dxo == 0 && dyo >= -3 && dyo <= 3) return 6 + xoff(dyo);
+            return -1;
+        default:
+            if (kk < 0 || kk >= W) return -1;
+            if (dyo == 0 && dxo >= -3 && dxo <= 3) return (dxo + 3) * 7 + kk;
+            if (dxo == 0 && dyo >= -3 && dyo <= 3) return 49 + xoff(dyo) * 7 + kk;
+            return -1;
+        }
+    }
+
+    // Row of the still-water operator (eta = 0, d = h) in slot form,
+    // following Eq. (16)-(18) with the push-forward of Eq. (9b) and (13b-13d).
+    void a0_row(int ix, int iy, int j, double *v) const {
+        for (int s = 0; s < nslot; ++s) v[s] = 0.0;
+        int c = iy * nx + ix;
+        if (j == nz - 1) { v[sigma_slot(layout, W - 1)] = 1.0; return; }
+        double d = h[c], f = 1.0 / d;
+        double gx = hx[c], gy = three_d ? hy[c] : 0.0;
+        bool box = layout == BOX2D || layout == BOX3D;
+        if (j == -1) {
+            double nrm = 1.0 / std::sqrt(1.0 + gx * gx + gy * gy);
+            double a0 = gx * f, a0y = gy * f;
+            double cs = -nrm * (gx * a0 + gy * a0y + f);
+            const double *w1 = &ws1[1 * W];   // sigma weights of level 0
+            for (int kk = 0; kk < W; ++kk) v[sigma_slot(layout, kk)] += cs * w1[kk];
+            if (box) {
+                for (int t = -HALF; t <= HALF; ++t) {
+                    if (t == 0) {
+                        v[sigma_slot(layout, 1)] += -nrm * gx * wx1[t + HALF] - nrm * gy * (three_d ? wy1[t + HALF] : 0.0);
+                        continue;
+                    }
+                    int s = find_slot(ix, iy, j, wrapx(ix + t), iy, 0);
+                    v[s] += -nrm * gx * wx1[t + HALF];
+                    if (three_d) {
+                        int s2 = find_slot(ix, iy, j, ix, wrapy(iy + t), 0);
+                        v[s2] += -nrm * gy * wy1[t + HALF];
+                    }
+                }
+            }
+            return;
+        }
+        double sg = (double)j / (nz - 1);
+        const double *w1 = &ws1[(j + 1) * W];
+        const double *w2 = &ws2[(j + 1) * W];
+        int w0 = win[j + 1];
+        double a = (gx - sg * hx[c]) * f;           // sigma_x (both stages equal at rest)
+        double as = -hx[c] * f;
+        double ax = (hxx[c] - sg * hxx[c] - a * hx[c]) * f;
+        double ay = 0, ays = 0, ayy = 0;
+        if (three_d) {
+            ay = (gy - sg * hy[c]) * f;
+            ays = -hy[c] * f;
+            ayy = (hyy[c] - sg * hyy[c] - ay * hy[c]) * f;
+        }
+        double c_ss = a * a + ay * ay + f * f;
+        double c_s = ax + a * as + ayy + ay * ays;
+        for (int t = -HALF; t <= HALF; ++t) {
+            int s = find_slot(ix, iy, j, wrapx(ix + t), iy, j);
+            v[s] += wx2[t + HALF];
+            if (three_d) {
+                int s2 = find_slot(ix, iy, j, ix, wrapy(iy + t), j);
+                v[s2] += wy2[t + HALF];
+            }
+        }
+        for (int kk = 0; kk < W; ++kk) v[sigma_slot(layout, kk)] += c_ss * w2[kk] + c_s * w1[kk];
+        if (box) {
+            for (int t = -HALF; t <= HALF; ++t)
+                for (int kk = 0; kk < W; ++kk) {
+                    int s = find_slot(ix, iy, j, wrapx(ix + t), iy, w0 + kk);
+                    v[s] += 2.0 * a * wx1[t + HALF] * w1[kk];
+                    if (three_d) {
+                        int s2 = find_slot(ix, iy, j, ix, wrapy(iy + t), w0 + kk);
+                        v[s2] += 2.0 * ay * wy1[t + HALF] * w1[kk];
+                    }
+                }
+        }
+    }
+};
+
+// ILU(0), row by row in rank order (IKJ form): for each row i and each entry
+// k < i of its pattern in increasing order, l_ik = a_ik / u_kk, then
+// a_ij -= l_ik u_kj for every j > k present in both row k and row i.
+static int factorise(const Host &H, std::vector<double> &lu, std::vector<double> &udinv) {
+    const int ns = H.nslot;
+    const long long m = H.m;
+    lu.assign((size_t)m * ns, 0.0);       // row-major during the factorisation
+    udinv.assign((size_t)m, 0.0);
+    std::vector<double> v(ns);
+    std::vector<std::pair<long long, int>> lower;
+    for (long long i = 0; i < m; ++i) {
+        int ix, iy, j;
+        H.node_of_rank(i, ix, iy, j);
+        H.a0_row(ix, iy, j, v.data());
+        lower.clear();
+        for (int s = 0; s < ns; ++s) {
+            if (!H.in_pattern(s, j)) { v[s] = 0.0; continue; }
+            int bx, by, bl;
+            H.slot_nb(s, ix, iy, j, bx, by, bl);
+            long long k = H.rank_of(bx, by, bl);
+            if (k < i) lower.push_back({k, s});
+        }
+        std::sort(lower.begin(), lower.end());
+        for (auto &ks : lower) {
+            long long k = ks.first;
+            int s = ks.second;
+            double l = v[s] * udinv[k];
+            v[s] = l;
+            int kx, ky, kj;
+            H.node_of_rank(k, kx, ky, kj);
+            const double *rowk = &lu[(size_t)k * ns];
+            for (int s2 = 0; s2 < ns; ++s2) {
+                if (!H.in_pattern(s2, kj)) continue;
+                int bx, by, bl;
+                H.slot_nb(s2, kx, ky, kj, bx, by, bl);
+                if (H.rank_of(bx, by, bl) <= k) continue;
+                int s3 = H.find_slot(ix, iy, j, bx, by, bl);
+                if (s3 < 0 || !H.in_pattern(s3, j)) continue;
+                v[s3] -= l * rowk[s2];
+            }
+        }
+        double ud = v[sigma_slot(H.layout, j - H.win[j + 1])];
+        if (ud == 0.0 || !std::isfinite(ud)) return SW_ERR_SINGULAR_PRECOND;
+        udinv[i] = 1.0 / ud;
+        std::copy(v.begin(), v.end(), lu.begin() + (size_t)i * ns);
+    }
+    return SW_OK;
+}
+
+}  // namespace
+
+static int dalloc(Problem *P, void **ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    P->allocs.push_back(*ptr);
+    e = cudaMemset(*ptr, 0, bytes ? bytes : 16);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    return SW_OK;
+}
+
+int setup_solver_launch(Problem *P);  // solver.cu
+
+}  // namespace sw
+
+using namespace sw;
+
+extern "C" const char *sw_last_error(void) { return g_err.c_str(); }
+
+extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, const double *h_depth,
+                                 sw_problem **out) {
+    if (!grid || !params || !h_depth || !out) { set_error("null argument"); return SW_ERR_BAD_ARG; }
+    *out = nullptr;
+    const sw_grid g = *grid;
+    const sw_params p = *params;
+    bool three_d = g.ny > 1;
+    if (g.nx < 8 || g.nx % 4 != 0 || g.ny < 1 || (three_d && (g.ny < 8 || g.ny % 4 != 0)) || g.nz < W ||
+        g.nz + 1 > MAX_LEVELS || !(g.lx > 0) || (three_d && !(g.ly > 0))) {
+        set_error("grid: need nx (and ny in 3-D) multiples of 4 and >= 8, 7 <= nz <= 63, positive lengths");
+        return SW_ERR_BAD_ARG;
+    }
+    if (p.restart < 1 || p.restart > MAX_RESTART || p.max_restarts < 0 || !(p.tol > 0) || p.guess < 0 ||
+        p.guess > 2 || p.k < 1 || p.k > MAX_K || !(p.decay > 0) || p.decay > 1 || p.n_init_solves < 0 ||
+        (p.precision != SW_PRECISION_FP64 && p.precision != SW_PRECISION_MIXED)) {
+        set_error("params: restart 1..32, k 1..16, decay in (0,1], tol > 0, known guess/precision");
+        return SW_ERR_BAD_ARG;
+    }
+    Host H;
+    H.nx = g.nx; H.ny = g.ny; H.nz = g.nz; H.P = g.nz + 1; H.ncol = g.nx * g.ny;
+    H.three_d = three_d;
+    H.m = (long long)H.ncol * H.P;
+    H.dx = g.lx / g.nx;
+    H.dy = three_d ? g.ly / g.ny : 1.0;
+    bool flat = true;
+    H.h.assign(h_depth, h_depth + H.ncol);
+    for (int c = 0; c < H.ncol; ++c) {
+        if (!(H.h[c] > 0) || !std::isfinite(H.h[c])) { set_error("depth must be positive"); return SW_ERR_BAD_ARG; }
+        if (H.h[c] != H.h[0]) flat = false;
+    }
+    H.layout = three_d ? (flat ? CROSS3D : BOX3D) : (flat ? CROSS2D : BOX2D);
+    H.nslot = layout_nslot(H.layout);
+    {
+        long double xs[W];
+        for (int t = 0; t < W; ++t) xs[t] = (long double)(t - HALF) * (long double)H.dx;
+        lagrange_weights(xs, 0.0L, H.wx1, H.wx2);
+        for (int t = 0; t < W; ++t) xs[t] = (long double)(t - HALF) * (long double)H.dy;
+        lagrange_weights(xs, 0.0L, H.wy1, H.wy2);
+        H.ws1.resize(H.P * W); H.ws2.resize(H.P * W); H.win.resize(H.P);
+        for (int j = -1; j < g.nz; ++j) {
+            int s0 = sigma_window(g.nz, j);
+            H.win[j + 1] = s0;
+            for (int k = 0; k < W; ++k) xs[k] = (long double)(s0 + k) / (long double)(g.nz - 1);
+            lagrange_weights(xs, (long double)j / (long double)(g.nz - 1), &H.ws1[(j + 1) * W], &H.ws2[(j + 1) * W]);
+        }
+    }
+    // surface-grid derivatives of the bathymetry (D_chi, D_gamma of Sec. 3)
+    H.hx.assign(H.ncol, 0.0); H.hy.assign(H.ncol, 0.0); H.hxx.assign(H.ncol, 0.0); H.hyy.assign(H.ncol, 0.0);
+    for (int iy = 0; iy < g.ny; ++iy)
+        for (int ix = 0; ix < g.nx; ++ix) {
+            double s1 = 0, s2 = 0, t1 = 0, t2 = 0;
+            for (int t = -HALF; t <= HALF; ++t) {
+                double vx = H.h[iy * g.nx + H.wrapx(ix + t)];
+                s1 += H.wx1[t + HALF] * vx;
+                s2 += H.wx2[t + HALF] * vx;
+                if (three_d) {
+                    double vy = H.h[H.wrapy(iy + t) * g.nx + ix];
+                    t1 += H.wy1[t + HALF] * vy;
+                    t2 += H.wy2[t + HALF] * vy;
+                }
+            }
+            int c = iy * g.nx + ix;
+            H.hx[c] = s1; H.hxx[c] = s2; H.hy[c] = t1; H.hyy[c] = t2;
+        }
+    std::vector<double> lu_rows, udinv;
+    int st = factorise(H, lu_rows, udinv);
+    if (st != SW_OK) { set_error("zero pivot in ILU(0)"); return st; }
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    Problem *P = new (std::nothrow) Problem();
+    if (!P) { set_error("out of host memory"); return SW_ERR_BAD_ARG; }
+    P->grid = g; P->params = p; P->device = dev;
+    P->phys.g = 9.81; P->phys.rho = 1000.0; P->phys.dt = 0.0;
+    P->m = H.m; P->ncol = H.ncol; P->P = H.P;
+    const long long m = H.m;
+    const int ns = H.nslot;
+    int rc = SW_OK;
+#define ALLOC(ptr, bytes) do { if ((rc = dalloc(P, (void **)&(ptr), (bytes))) != SW_OK) { sw_destroy_problem((sw_problem *)P); return rc; } } while (0)
+    // weights: wx1, wx2, wy1, wy2, ws1 (P*7), ws2 (P*7)
+    std::vector<double> wts(4 * W + 2 * H.P * W);
+    std::copy(H.wx1, H.wx1 + W, wts.begin());
+    std::copy(H.wx2, H.wx2 + W, wts.begin() + W);
+    std::copy(H.wy1, H.wy1 + W, wts.begin() + 2 * W);
+    std::copy(H.wy2, H.wy2 + W, wts.begin() + 3 * W);
+    std::copy(H.ws1.begin(), H.ws1.end(), wts.begin() + 4 * W);
+    std::copy(H.ws2.begin(), H.ws2.end(), wts.begin() + 4 * W + H.P * W);
+    ALLOC(P->d_weights, wts.size() * sizeof(double));
+    ALLOC(P->d_win, H.P * sizeof(int));
+    ALLOC(P->d_hcols, 5 * (size_t)H.ncol * sizeof(double));
+    ALLOC(P->d_geom, 20 * (size_t)H.ncol * sizeof(double));
+    ALLOC(P->d_lu64, (size_t)m * ns * sizeof(double));
+    ALLOC(P->d_udinv64, (size_t)m * sizeof(double));
+    ALLOC(P->d_lu32, (size_t)m * ns * sizeof(float));
+    ALLOC(P->d_udinv32, (size_t)m * sizeof(float));
+    ALLOC(P->d_V, (size_t)(p.restart + 1) * m * sizeof(double));
+    if (p.precision == SW_PRECISION_MIXED) ALLOC(P->d_V32, (size_t)(p.restart + 1) * m * sizeof(float));
+    ALLOC(P->d_work, 6 * (size_t)m * sizeof(double));
+    ALLOC(P->d_Y[0], (size_t)p.k * m * sizeof(double));
+    ALLOC(P->d_Y[1], (size_t)p.k * m * sizeof(double));
+    ALLOC(P->d_W, (size_t)p.k * m * sizeof(double));
+    ALLOC(P->d_xprev, (size_t)m * sizeof(double));
+    ALLOC(P->d_omega, MAX_K * sizeof(double));
+    ALLOC(P->d_stats, sizeof(DevStats));
+    ALLOC(P->d_host_io, (3 * (size_t)m + 2 * (size_t)H.ncol) * sizeof(double));
+    e = cudaMemcpy(P->d_weights, wts.data(), wts.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_win, H.win.data(), H.P * sizeof(int), cudaMemcpyHostToDevice);
+    std::vector<double> hc(5 * (size_t)H.ncol);
+    std::copy(H.h.begin(), H.h.end(), hc.begin());
+    std::copy(H.hx.begin(), H.hx.end(), hc.begin() + H.ncol);
+    std::copy(H.hy.begin(), H.hy.end(), hc.begin() + 2 * H.ncol);
+    std::copy(H.hxx.begin(), H.hxx.end(), hc.begin() + 3 * H.ncol);
+    std::copy(H.hyy.begin(), H.hyy.end(), hc.begin() + 4 * H.ncol);
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_hcols, hc.data(), hc.size() * sizeof(double), cudaMemcpyHostToDevice);
+    // factors slot-major on the device: lu[s * m + rank]
+    {
+        std::vector<double> t((size_t)m * ns);
+        std::vector<float> t32((size_t)m * ns);
+        for (long long i = 0; i < m; ++i)
+            for (int s = 0; s < ns; ++s) {
+                double v = lu_rows[(size_t)i * ns + s];
+                t[(size_t)s * m + i] = v;
+                t32[(size_t)s * m + i] = (float)v;
+            }
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_lu64, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_lu32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+        std::vector<float> u32(udinv.size());
+        for (size_t i = 0; i < udinv.size(); ++i) u32[i] = (float)udinv[i];
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_udinv64, udinv.data(), m * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_udinv32, u32.data(), m * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) { sw_destroy_problem((sw_problem *)P); return cuda_fail(e, "upload"); }
+    Dev &D = P->dev;
+    D.nx = g.nx; D.ny = g.ny; D.nz = g.nz; D.P = H.P; D.ncol = H.ncol; D.three_d = three_d;
+    D.layout = H.layout; D.nslot = ns; D.m = m; D.dx = H.dx; D.dy = H.dy;
+    D.wx1 = P->d_weights; D.wx2 = P->d_weights + W; D.wy1 = P->d_weights + 2 * W; D.wy2 = P->d_weights + 3 * W;
+    D.ws1 = P->d_weights + 4 * W; D.ws2 = P->d_weights + 4 * W + H.P * W;
+    D.win = P->d_win;
+    D.h = P->d_hcols; D.hx = P->d_hcols + H.ncol; D.hy = P->d_hcols + 2 * H.ncol;
+    D.hxx = P->d_hcols + 3 * H.ncol; D.hyy = P->d_hcols + 4 * H.ncol;
+    D.gp = P->d_geom;
+    D.lu64 = P->d_lu64; D.lu32 = P->d_lu32; D.udinv64 = P->d_udinv64; D.udinv32 = P->d_udinv32;
+    rc = setup_solver_launch(P);
+    if (rc != SW_OK) { sw_destroy_problem((sw_problem *)P); return rc; }
+    ALLOC(P->d_part, (size_t)P->nblocks * 2 * 160 * sizeof(double) + 8192);
+    ALLOC(P->d_sync, 256);
+#undef ALLOC
+    *out = (sw_problem *)P;
+    return SW_OK;
+}
+
+extern "C" int sw_destroy_problem(sw_problem *pp) {
+    Problem *P = (Problem *)pp;
+    if (!P) return SW_OK;
+    for (void *a : P->allocs) cudaFree(a);
+    delete P;
+    return SW_OK;
+}
+
+extern "C" int sw_problem_size(const sw_problem *pp, long long *m) {
+    if (!pp || !m) { set_error("null argument"); return SW_ERR_BAD_ARG; }
+    *m = ((const Problem *)pp)->m;
+    return SW_OK;
+}
+
+// Gaussian sketch vectors: SplitMix64 (Steele, Lea & Flood 2014) as a
+// counter-based generator, two outputs per value through Box-Muller.
+static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + i * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+extern "C" int sw_draw_omega(uint64_t seed, long long solve_index, int k, double *h_omega) {
+    if (!h_omega || k < 1 || solve_index < 0) { set_error("bad argument"); return SW_ERR_BAD_ARG; }
+    const double inv53 = 1.0 / 9007199254740992.0;
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int c = 0; c < k; ++c) {
+        uint64_t base = 2 * ((uint64_t)solve_index * (uint64_t)k + (uint64_t)c) + 1;
+        double u1 = ((double)(splitmix64_at(seed, base) >> 11) + 1.0) * inv53;
+        double u2 = (double)(splitmix64_at(seed, base + 1) >> 11) * inv53;
+        double r = std::sqrt(-2.0 * std::log(u1));
+        double th = two_pi * u2;
+        h_omega[c] = r * std::cos(th);
+    }
+    return SW_OK;
+}

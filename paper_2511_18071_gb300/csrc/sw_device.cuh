@@ -1,0 +1,450 @@
+// Device building blocks of the solver: column geometry, the matrix-free
+// mixed-stage operator, the colour-ordered ILU(0) sweeps and grid reductions.
+//
+// FP64 on this GPU issues one warp instruction per ~32 ns per SM sub-partition
+// whatever the number of active lanes, so the code below counts FP64 warp
+// instructions rather than lanes: sums over many values are done with a
+// reduce-scatter across lanes (about one add per value per warp) instead of a
+// shuffle tree per value (five adds per value).
+#pragma once
+#include <cooperative_groups.h>
+
+#include "sw_internal.cuh"
+
+namespace sw {
+namespace cg = cooperative_groups;
+
+constexpr int NTHREADS = 256;
+constexpr int NWARPS = NTHREADS / 32;
+constexpr int NCC = 19;   // per-column coefficients written by the geometry step
+constexpr int PART_STRIDE = 160;  // values per block in the partial-sum buffer
+
+// Column coefficient slots (each an array of ncol doubles in Dev::gp).
+enum {
+    CC_F = 0,      // 1/d at stage i-1
+    CC_E,          // 1/d at stage i
+    CC_EF,         // e f
+    CC_AP0,        // h_x f           (sigma_x^(i-1) = AP0 - sigma AP1)
+    CC_AP1,        // d_x^(i-1) f
+    CC_AXP0,       // h_xx f          (d sigma_x^(i-1)/d chi = AXP0 - sigma AXP1 - sigma_x AP1)
+    CC_AXP1,       // d_xx^(i-1) f
+    CC_BP0,        // h_x e           (sigma_x^(i) = BP0 - sigma BP1)
+    CC_BP1,        // d_x^(i) e
+    CC_GS,         // ghost row: coefficient of D_sigma p at the bed
+    CC_GX,         // ghost row: coefficient of D_chi p at the bed
+    CC_GY,         // ghost row: coefficient of D_gamma p at the bed
+    CC_AY0, CC_AY1, CC_AYY0, CC_AYY1, CC_BY0, CC_BY1,  // y counterparts (3-D)
+    CC_GN          // ghost row: -1/|(h_x, h_y, 1)|, the vertical component of the unit normal
+};
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ---------------------------------------------------------------------------
+// a1: geometry.  For eta^(i-1) and eta^(i): d = h + eta, its surface
+// derivatives with the fixed 7-point operators (Sec. 3), and the per-column
+// factors of sigma_x, sigma_y and 1/d used by every row (Eq. 13b-13d).
+// ---------------------------------------------------------------------------
+__device__ inline void geometry_columns(const Dev &D, const double *eta_prev, const double *eta_cur, int tid,
+                                        int nth) {
+    double *cc = D.gp;
+    const int n = D.ncol;
+    for (int c = tid; c < n; c += nth) {
+        int ix = c % D.nx, iy = c / D.nx;
+        double dp1 = 0, dp2 = 0, dc1 = 0, dpy1 = 0, dpy2 = 0, dcy1 = 0;
+#pragma unroll
+        for (int t = -HALF; t <= HALF; ++t) {
+            int cx = iy * D.nx + wrapi(ix + t, D.nx);
+            double vp = D.h[cx] + eta_prev[cx];
+            double vc = D.h[cx] + eta_cur[cx];
+            dp1 += D.wx1[t + HALF] * vp;
+            dp2 += D.wx2[t + HALF] * vp;
+            dc1 += D.wx1[t + HALF] * vc;
+            if (D.three_d) {
+                int cy = wrapi(iy + t, D.ny) * D.nx + ix;
+                double wp = D.h[cy] + eta_prev[cy];
+                double wc = D.h[cy] + eta_cur[cy];
+                dpy1 += D.wy1[t + HALF] * wp;
+                dpy2 += D.wy2[t + HALF] * wp;
+                dcy1 += D.wy1[t + HALF] * wc;
+            }
+        }
+        double dp = D.h[c] + eta_prev[c], dcu = D.h[c] + eta_cur[c];
+        double f = 1.0 / dp, e = 1.0 / dcu;
+        double hx = D.hx[c], hy = D.three_d ? D.hy[c] : 0.0;
+        cc[CC_F * n + c] = f;
+        cc[CC_E * n + c] = e;
+        cc[CC_EF * n + c] = e * f;
+        cc[CC_AP0 * n + c] = hx * f;
+        cc[CC_AP1 * n + c] = dp1 * f;
+        cc[CC_AXP0 * n + c] = D.hxx[c] * f;
+        cc[CC_AXP1 * n + c] = dp2 * f;
+        cc[CC_BP0 * n + c] = hx * e;
+        cc[CC_BP1 * n + c] = dc1 * e;
+        // ghost row n . grad^(i-1) p at sigma = 0 with n = -(h_x, h_y, 1)/|(h_x, h_y, 1)|
+        double nrm = 1.0 / sqrt(1.0 + hx * hx + hy * hy);
+        cc[CC_GS * n + c] = -nrm * (hx * hx * f + hy * hy * f + f);
+        cc[CC_GX * n + c] = -nrm * hx;
+        cc[CC_GY * n + c] = -nrm * hy;
+        cc[CC_GN * n + c] = -nrm;
+        if (D.three_d) {
+            cc[CC_AY0 * n + c] = hy * f;
+            cc[CC_AY1 * n + c] = dpy1 * f;
+            cc[CC_AYY0 * n + c] = D.hyy[c] * f;
+            cc[CC_AYY1 * n + c] = dpy2 * f;
+            cc[CC_BY0 * n + c] = hy * e;
+            cc[CC_BY1 * n + c] = dcy1 * e;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a2: matrix-free operator y = A(eta^(i-1), eta^(i)) p (Eq. 16-18).
+// One tile = TX x TY columns, all levels.  p and q = D_sigma p are staged in
+// shared memory for the tile plus a 3-column halo, so each q value is computed
+// once and reused by the 7 rows that need it for the mixed derivative
+// D_chi D_sigma.  Interior rows:
+//   p_xx + p_yy + (a+b) p_xs + (a'+b') p_ys + (a b + a' b' + e f) p_ss
+//        + (a_x + b a_s + a'_y + b' a'_s) p_s
+// with a = sigma_x^(i-1), b = sigma_x^(i) (the chain rule applied to the
+// push-forward of Eq. 9b); ghost rows the Neumann condition of Eq. (17) at the
+// bed; surface rows the identity (p = 0 on the free surface).
+// ---------------------------------------------------------------------------
+struct Tiling {
+    int TX, TY, HX, HY, HW, ntx, nty, ntiles;
+};
+
+template <typename T, class Loader, class Store>
+__device__ inline void apply_tile(const Dev &D, const Tiling &tl, int tile, T *sp, T *sq, Loader &ld, Store &st) {
+    const int P = D.P, HX = tl.HX, HY = tl.HY, HW = tl.HW;
+    const int tx0 = (tile % tl.ntx) * tl.TX;
+    const int ty0 = (tile / tl.ntx) * tl.TY;
+    const int tid = threadIdx.x;
+    // stage p on tile + halo
+    for (int idx = tid; idx < P * HW; idx += blockDim.x) {
+        int l = idx / HW, r = idx - l * HW;
+        int a = r % HX, b = r / HX;
+        bool hxo = a < HALF || a >= HX - HALF;
+        bool hyo = D.three_d && (b < HALF || b >= HY - HALF);
+        T v = T(0);
+        if (!(hxo && hyo)) {
+            int gx = wrapi(tx0 + a - HALF, D.nx);
+            int gy = D.three_d ? wrapi(ty0 + b - HALF, D.ny) : 0;
+            v = ld((long long)l * D.ncol + gy * D.nx + gx);
+        }
+        sp[idx] = v;
+    }
+    __syncthreads();
+    // q = D_sigma p on tile + halo
+    for (int idx = tid; idx < P * HW; idx += blockDim.x) {
+        int l = idx / HW, r = idx - l * HW;
+        const double *w1 = D.ws1 + l * W;
+        int base = (D.win[l] + 1) * HW + r;
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < W; ++k) s += T(w1[k]) * sp[base + k * HW];
+        sq[idx] = s;
+    }
+    __syncthreads();
+    const int n = D.ncol;
+    const T inv_nzm1 = T(1.0 / (D.nz - 1));
+    const double *cc = D.gp;
+    for (int idx = tid; idx < P * tl.TX * tl.TY; idx += blockDim.x) {
+        int l = idx / (tl.TX * tl.TY), r = idx - l * (tl.TX * tl.TY);
+        int a = r % tl.TX + HALF, b = D.three_d ? r / tl.TX + HALF : 0;
+        int gx = tx0 + a - HALF, gy = D.three_d ? ty0 + b - HALF : 0;
+        int c = gy * D.nx + gx;
+        int hr = b * HX + a;
+        long long node = (long long)l * n + c;
+        T y;
+        if (l == P - 1) {
+            y = sp[l * HW + hr];
+        } else if (l == 0) {
+            // ghost row at the bed (level index 1)
+            T px = T(0), py = T(0);
+#pragma unroll
+            for (int t = -HALF; t <= HALF; ++t) {
+                px += T(D.wx1[t + HALF]) * sp[HW + hr + t];
+                if (D.three_d) py += T(D.wy1[t + HALF]) * sp[HW + hr + t * HX];
+            }
+            y = T(cc[CC_GS * n + c]) * sq[HW + hr] + T(cc[CC_GX * n + c]) * px;
+            if (D.three_d) y += T(cc[CC_GY * n + c]) * py;
+        } else {
+            T sg = T(l - 1) * inv_nzm1;
+            T ap1 = T(cc[CC_AP1 * n + c]);
+            T aa = T(cc[CC_AP0 * n + c]) - sg * ap1;
+            T bb = T(cc[CC_BP0 * n + c]) - sg * T(cc[CC_BP1 * n + c]);
+            T ax = T(cc[CC_AXP0 * n + c]) - sg * T(cc[CC_AXP1 * n + c]) - aa * ap1;
+            T c_xs = aa + bb;
+            T c_ss = aa * bb + T(cc[CC_EF * n + c]);
+            T c_s = ax - bb * ap1;
+            const T *pl = sp + l * HW + hr;
+            const T *ql = sq + l * HW + hr;
+            T pxx = T(0), pxs = T(0);
+#pragma unroll
+            for (int t = -HALF; t <= HALF; ++t) {
+                pxx += T(D.wx2[t + HALF]) * pl[t];
+                pxs += T(D.wx1[t + HALF]) * ql[t];
+            }
+            const double *w2 = D.ws2 + l * W;
+            const T *pc = sp + (D.win[l] + 1) * HW + hr;
+            T pss = T(0);
+#pragma unroll
+            for (int k = 0; k < W; ++k) pss += T(w2[k]) * pc[k * HW];
+            y = pxx + c_xs * pxs + c_s * ql[0];
+            if (D.three_d) {
+                T ay1 = T(cc[CC_AY1 * n + c]);
+                T ay = T(cc[CC_AY0 * n + c]) - sg * ay1;
+                T by = T(cc[CC_BY0 * n + c]) - sg * T(cc[CC_BY1 * n + c]);
+                T ayy = T(cc[CC_AYY0 * n + c]) - sg * T(cc[CC_AYY1 * n + c]) - ay * ay1;
+                c_ss += ay * by;
+                T c_ys = ay + by;
+                T c_sy = ayy - by * ay1;
+                T pyy = T(0), pys = T(0);
+#pragma unroll
+                for (int t = -HALF; t <= HALF; ++t) {
+                    pyy += T(D.wy2[t + HALF]) * pl[t * HX];
+                    pys += T(D.wy1[t + HALF]) * ql[t * HX];
+                }
+                y += pyy + c_ys * pys + c_sy * ql[0];
+            }
+            y += c_ss * pss;
+        }
+        st(node, y);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// a3: preconditioner sweeps.  Rank order = colour, column, level.  A warp
+// owns one column; lane l holds levels l-1 and l+31.  The forward sweep of
+// colour c first subtracts the couplings to columns of lower colours (final
+// already), then runs the in-column recurrence level by level, broadcasting
+// each new value with a shuffle.  The backward sweep mirrors it with the
+// upper factor and higher colours.  In place on `out`.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int col_of(const Dev &D, int c, int q) {
+    if (!D.three_d) return c + 4 * q;
+    int per_row = D.nx >> 2;
+    int iy = q / per_row;
+    int ix = ((c - iy) & 3) + 4 * (q - iy * per_row);
+    return iy * D.nx + ix;
+}
+
+// Neighbour (column, level) of slot s for a row at (ix, iy, j); returns false
+// for the in-column sigma slots.
+__device__ __forceinline__ bool off_slot(const Dev &D, int s, int ix, int iy, int j, int &col, int &lev) {
+    int ox = 0, oy = 0;
+    int w0 = D.win[j + 1];
+    switch (D.layout) {
+    case CROSS2D:
+        if (s >= 6) return false;
+        ox = s < 3 ? s - 3 : s - 2; lev = j; break;
+    case BOX2D:
+        ox = s / 7 - 3; if (ox == 0) return false; lev = w0 + s % 7; break;
+    case CROSS3D:
+        if (s >= 12) return false;
+        if (s < 6) ox = s < 3 ? s - 3 : s - 2; else { int u = s - 6; oy = u < 3 ? u - 3 : u - 2; }
+        lev = j; break;
+    default:
+        if (s < 49) { ox = s / 7 - 3; if (ox == 0) return false; lev = w0 + s % 7; }
+        else { int u = (s - 49) / 7; oy = u < 3 ? u - 3 : u - 2; lev = w0 + (s - 49) % 7; }
+    }
+    int gx = wrapi(ix + ox, D.nx);
+    int gy = D.three_d ? wrapi(iy + oy, D.ny) : 0;
+    col = gy * D.nx + gx;
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ const T *lu_ptr(const Dev &D);
+template <> __device__ __forceinline__ const double *lu_ptr<double>(const Dev &D) { return D.lu64; }
+template <> __device__ __forceinline__ const float *lu_ptr<float>(const Dev &D) { return D.lu32; }
+template <typename T>
+__device__ __forceinline__ const T *udinv_ptr(const Dev &D);
+template <> __device__ __forceinline__ const double *udinv_ptr<double>(const Dev &D) { return D.udinv64; }
+template <> __device__ __forceinline__ const float *udinv_ptr<float>(const Dev &D) { return D.udinv32; }
+
+__device__ __forceinline__ int colour_of(const Dev &D, int col) {
+    int ix = col % D.nx, iy = col / D.nx;
+    return (ix + iy) & 3;
+}
+
+// forward (lower) sweep of one column of colour c; in -> out
+template <typename T, typename TI>
+__device__ inline void ilu_fwd_column(const Dev &D, int c, int q, const TI *in, T *out, int lane) {
+    const T *lu = lu_ptr<T>(D);
+    const long long m = D.m;
+    const int col = col_of(D, c, q);
+    const int ix = col % D.nx, iy = col / D.nx;
+    const long long rbase = ((long long)c * (D.ncol >> 2) + q) * D.P;
+    T g[2];
+    int jl[2] = {lane - 1, lane + 31};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int j = jl[h];
+        g[h] = T(0);
+        if (j >= D.nz) continue;
+        long long r = rbase + j + 1;
+        T acc = T(in[(long long)(j + 1) * D.ncol + col]);
+        for (int s = 0; s < D.nslot; ++s) {
+            int nc, lev;
+            if (!off_slot(D, s, ix, iy, j, nc, lev)) continue;
+            if (colour_of(D, nc) >= c) continue;
+            acc -= lu[(long long)s * m + r] * out[(long long)(lev + 1) * D.ncol + nc];
+        }
+        g[h] = acc;
+    }
+    // in-column recurrence
+    T lsig[2][W];
+    int w0[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int j = jl[h];
+        w0[h] = (j < D.nz) ? D.win[j + 1] : 0;
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            lsig[h][k] = (j < D.nz) ? lu[(long long)sigma_slot(D.layout, k) * m + rbase + j + 1] : T(0);
+    }
+    for (int jj = -1; jj < D.nz; ++jj) {
+        int owner = (jj + 1) & 31, which = (jj + 1) >> 5;
+        T mine = which ? g[1] : g[0];
+        T yjj = __shfl_sync(0xffffffffu, mine, owner);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int j = jl[h];
+            int kk = jj - w0[h];
+            if (j < D.nz && jj < j && kk >= 0) g[h] -= lsig[h][kk] * yjj;
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int j = jl[h];
+        if (j < D.nz) out[(long long)(j + 1) * D.ncol + col] = g[h];
+    }
+}
+
+// backward (upper) sweep of one column of colour c; in place on out
+template <typename T>
+__device__ inline void ilu_bwd_column(const Dev &D, int c, int q, T *out, int lane) {
+    const T *lu = lu_ptr<T>(D);
+    const T *udi = udinv_ptr<T>(D);
+    const long long m = D.m;
+    const int col = col_of(D, c, q);
+    const int ix = col % D.nx, iy = col / D.nx;
+    const long long rbase = ((long long)c * (D.ncol >> 2) + q) * D.P;
+    T g[2], ud[2];
+    int jl[2] = {lane - 1, lane + 31};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int j = jl[h];
+        g[h] = T(0);
+        ud[h] = T(0);
+        if (j >= D.nz) continue;
+        long long r = rbase + j + 1;
+        ud[h] = udi[r];
+        T acc = out[(long long)(j + 1) * D.ncol + col];
+        for (int s = 0; s < D.nslot; ++s) {
+            int nc, lev;
+            if (!off_slot(D, s, ix, iy, j, nc, lev)) continue;
+            if (colour_of(D, nc) <= c) continue;
+            acc -= lu[(long long)s * m + r] * out[(long long)(lev + 1) * D.ncol + nc];
+        }
+        g[h] = acc;
+    }
+    T usig[2][W];
+    int w0[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int j = jl[h];
+        w0[h] = (j < D.nz) ? D.win[j + 1] : 0;
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            usig[h][k] = (j < D.nz) ? lu[(long long)sigma_slot(D.layout, k) * m + rbase + j + 1] : T(0);
+    }
+    T xv[2] = {T(0), T(0)};
+    for (int jj = D.nz - 1; jj >= -1; --jj) {
+        int owner = (jj + 1) & 31, which = (jj + 1) >> 5;
+        T cand = which ? g[1] * ud[1] : g[0] * ud[0];
+        T xjj = __shfl_sync(0xffffffffu, cand, owner);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int j = jl[h];
+            if (j >= D.nz) continue;
+            if (j == jj) xv[h] = xjj;
+            int kk = jj - w0[h];
+            if (jj > j && kk < W) g[h] -= usig[h][kk] * xjj;
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int j = jl[h];
+        if (j < D.nz) out[(long long)(j + 1) * D.ncol + col] = xv[h];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions.  Each thread holds up to N partial sums; the block reduces them
+// with a reduce-scatter inside each warp (lane i ends with the warp's sum of
+// value i), then across warps through shared memory, and writes one partial
+// per value and block to part[v * nblocks + block].
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void warp_reduce_scatter(double (&v)[N], int lane) {
+    static_assert(N == 32, "reduce-scatter over 32 values");
+    // after the step with offset o a lane keeps the values whose bit o matches its lane bit
+#pragma unroll
+    for (int o = 16, cnt = 16; o >= 1; o >>= 1, cnt >>= 1) {
+        bool upper = lane & o;
+#pragma unroll
+        for (int i = 0; i < cnt; ++i) {
+            // pair (i, i + cnt): keep i if lower half, i + cnt if upper half
+            double send = upper ? v[i] : v[i + cnt];
+            double keep = upper ? v[i + cnt] : v[i];
+            double recv = __shfl_xor_sync(0xffffffffu, send, o);
+            v[i] = keep + recv;
+        }
+    }
+    // v[0] of lane l now holds the warp sum of value l: at the step with offset
+    // o the kept index gains bit o exactly when lane bit o is set.
+}
+
+// Block-reduce n <= 32 values (v[i], i >= n ignored) into part[v * nb + blockIdx.x].
+__device__ inline void block_partials32(double (&v)[32], int n, double *red, double *part, int nb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (n <= 4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i >= n) break;
+            double s = v[i];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) red[warp * 32 + i] = s;
+        }
+    } else {
+        warp_reduce_scatter<32>(v, lane);
+        red[warp * 32 + lane] = v[0];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double s = 0.0;
+        if (lane < n)
+            for (int w = 0; w < NWARPS; ++w) s += red[w * 32 + lane];
+        if (lane < n) part[lane * nb + blockIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// After a grid barrier: every block sums value i over the blocks into out[i].
+__device__ inline void gather_partials(const double *part, int n, int nb, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < n; i += NWARPS) {
+        double s = 0.0;
+        for (int b = lane; b < nb; b += 32) s += part[i * nb + b];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[i] = s;
+    }
+    __syncthreads();
+}
+
+}  // namespace sw

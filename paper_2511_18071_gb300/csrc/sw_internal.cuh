@@ -1,0 +1,104 @@
+// Internal definitions of libsawave: the device-side problem descriptor, the
+// ILU slot layout, and host-side bookkeeping.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/sawave.h"
+
+namespace sw {
+
+constexpr int W = 7;     // stencil width (sixth order, Sec. 5.2)
+constexpr int HALF = 3;
+constexpr int MAX_LEVELS = 64;      // nz + 1 <= 64 (two levels per lane in the ILU column sweeps)
+constexpr int MAX_RESTART = 32;
+constexpr int MAX_K = 16;
+
+// Sparsity layouts of the preconditioner rows ("slots").
+//   CROSS2D: x neighbours at the row's own level (6), sigma window (7)        -> 13
+//   BOX2D:   (dx, window level) for dx in -3..3 (7 x 7)                        -> 49
+//   CROSS3D: x (6) and y (6) neighbours at the own level, sigma window (7)     -> 19
+//   BOX3D:   x box (7 x 7) and y box without its centre column (6 x 7)         -> 91
+enum Layout { CROSS2D = 0, BOX2D = 1, CROSS3D = 2, BOX3D = 3 };
+
+__host__ __device__ inline int layout_nslot(int L) {
+    return L == CROSS2D ? 13 : L == BOX2D ? 49 : L == CROSS3D ? 19 : 91;
+}
+// Slot holding the sigma-window entry kk (same column).
+__host__ __device__ inline int sigma_slot(int L, int kk) {
+    return (L == CROSS2D ? 6 : L == CROSS3D ? 12 : 21) + kk;
+}
+
+// Device view of one problem (plain pointers; passed to kernels by value).
+struct Dev {
+    int nx, ny, nz, P, ncol, three_d, layout, nslot;
+    long long m;
+    double dx, dy;
+    const double *wx1, *wx2, *wy1, *wy2;   // 7 each
+    const double *ws1, *ws2;               // P x 7, row j+1
+    const int *win;                        // P, first level of the sigma window of level j
+    const double *h, *hx, *hy, *hxx, *hyy; // ncol
+    double *gp;                            // per-column coefficients of the current geometry pair
+    const double *lu64;                    // nslot x m (rank-major), FP64 factors
+    const float *lu32;                     // same, FP32 copy (mixed precision)
+    const double *udinv64;                 // 1 / u_jj per rank
+    const float *udinv32;
+};
+
+struct Problem {
+    sw_grid grid;
+    sw_params params;
+    sw_physics phys;
+    int device;
+    Dev dev;
+    long long m;
+    int ncol, P;
+    // device allocations
+    std::vector<void *> allocs;
+    double *d_weights = nullptr;
+    int *d_win = nullptr;
+    double *d_hcols = nullptr;     // h, hx, hy, hxx, hyy
+    double *d_geom = nullptr;      // per-column coefficients (20 x ncol)
+    double *d_lu64 = nullptr, *d_udinv64 = nullptr;
+    float *d_lu32 = nullptr, *d_udinv32 = nullptr;
+    double *d_V = nullptr;         // (restart + 1) x m Krylov basis
+    float *d_V32 = nullptr;
+    double *d_work = nullptr;      // 6 x m work vectors
+    double *d_Y[2] = {nullptr, nullptr};  // EWMA sketch, double buffered
+    double *d_W = nullptr;         // k x m, A Y
+    double *d_xprev = nullptr;
+    double *d_part = nullptr;      // per-block partial sums
+    double *d_omega = nullptr;     // k doubles
+    void *d_stats = nullptr;       // DevStats
+    void *d_sync = nullptr;        // grid barrier / flags
+    // stage driver state
+    double *d_u = nullptr, *d_v = nullptr, *d_w = nullptr, *d_eta = nullptr;
+    double *d_Ku = nullptr, *d_Kv = nullptr, *d_Kw = nullptr, *d_Keta = nullptr;
+    double *d_p = nullptr, *d_rhs = nullptr, *d_eta_new = nullptr, *d_feta = nullptr;
+    double *d_drv = nullptr;       // driver scratch (several fields)
+    double *d_host_io = nullptr;   // staging for the host-buffer entry point
+    int ybuf = 0;                  // which sketch buffer holds Y
+    bool pending = false;          // Y still lacks the newest solution (folded in by the next solve)
+    long long n_solves = 0;
+    long long total_iterations = 0;
+    int stage = 0;                 // next Runge-Kutta stage, 0..4
+    int nblocks = 0, nthreads = 0;
+    size_t smem = 0;
+    cudaStream_t last_stream = nullptr;
+    bool has_state = false;
+};
+
+// Statistics written by the device at the end of a solve.
+struct DevStats {
+    int iterations, restarts, converged, status;
+    double res0, res_final, true_res, guess_res, bnorm, braw;
+    int guess_rank, guess_mode, cholesky_shift, pad;
+    long long total_iterations;
+};
+
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace sw
