@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark: Poisson solves per second at relative residual 1e-8 on the steep
+periodic 2-D wave (512 x 17 sigma grid, kh = 2, four harmonics with
+a_n = a1 0.3^(n-1), a1/h = 0.08), subspace-accelerated (EWMA, k = 10, r = 0.9)
+against the plain FP64 cold start, with GMRES iterations per solve.
+
+One step = one LSERK45 time step = 5 stages, each stage the full hot path:
+right-hand side and Runge-Kutta updates, geometry, subspace guess (sketch
+update, W = A Y, Gram, CholeskyQR2, x0 = Y z) and restarted GMRES.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sawave|reference]
+For N > 1 run it under torch.distributed.run: every rank advances its own
+replica of the workload (the method has no exchange step across replicas).
+Prints one JSON line on rank 0.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solves/s at rel. residual 1e-8: accelerated vs plain; GMRES iters/solve"
+UNIT = "solves/s"
+WORKLOAD = "stokes2d_512x17_kh2_a1h0.08"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--impl", default="sawave", choices=["sawave", "reference"])
+    ap.add_argument("--decay", type=float, default=0.9)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    import workloads as W
+    return W.stokes_like_2d(nx=512, nz=17, kh=2.0, a1_over_h=0.08, steps=1000)
+
+
+def solver_kw(args, guess):
+    return dict(restart=20, max_restarts=500, tol=1e-8, guess=guess, k=args.k, decay=args.decay, n_init_solves=30,
+                seed=2511)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, serial, on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_run(args, warm_steps, timed_steps, budget_s=None):
+    import numpy as np
+
+    import oracle as O
+    import workloads as W
+    wl = workload()
+    kw = solver_kw(args, "ewma")
+    P = O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
+    st = W.state_arrays(wl)
+    phys = (wl["g"], wl["rho"], wl["dt"])
+    for _ in range(warm_steps):
+        for i in range(1, 6):
+            P.stage(phys, i, st)
+    its, n, t0 = 0, 0, time.perf_counter()
+    for s in range(timed_steps):
+        for i in range(1, 6):
+            _, stt, _ = P.stage(phys, i, st)
+            its += stt["iterations"]
+            n += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return n / dt, its / max(n, 1), n, dt
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    rate, its, n, dt = oracle_run(args, args.warmup, args.steps, budget_s=150.0)
+    line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 5000.0 * dt / n if n else None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "iters_per_solve": its,
+            "config": {"workload": WORKLOAD, "guess": "ewma", "k": args.k, "decay": args.decay, "tol": 1e-8,
+                       "restart": 20},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d solves after %d warm-up steps (stopped after 150 s)" % (n, args.warmup)},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2511_18071_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def profile_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = d.get(kernel)
+    if not ent or ent.get("source_sha") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def run_steps(sw, torch, prob, nsteps, flush=None, events=None):
+    h = prob.handle
+    for _ in range(nsteps):
+        if flush is not None:
+            flush.zero_()
+        if events is not None:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+        for _ in range(5):
+            sw.advance_stage(h)
+        if events is not None:
+            b.record()
+            events.append((a, b))
+
+
+def gpu_arm(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2511_18071_gb300 as sw
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    wl = workload()
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+
+    def make(guess):
+        P = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **solver_kw(args, guess))
+        sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+        sw.set_state(P.handle, t(wl["u"]), None, t(wl["w"]), t(wl["eta"]))
+        return P
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    # ---- accelerated (EWMA) ----
+    P = make("ewma")
+    run_steps(sw, torch, P, args.warmup)
+    torch.cuda.synchronize()
+    s0 = sw.get_stats(P.handle)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sw.enable_timing(P.handle, True)
+    events = []
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    gpu_index = int(vis[local_rank]) if local_rank < len(vis) and vis[local_rank].strip().isdigit() else local_rank
+    with ClockSampler(gpu_index) as clk:
+        wall0 = time.perf_counter()
+        run_steps(sw, torch, P, args.steps, flush=flush, events=events)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in events]
+    total_ms = sum(step_ms)
+    solve_ms, n_timed = sw.get_solve_time(P.handle)
+    sw.enable_timing(P.handle, False)
+    s1 = sw.get_stats(P.handle)
+    nsolves = 5 * args.steps
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * nsolves / (total_ms / 1e3)
+    its = (s1["total_iterations"] - s0["total_iterations"]) / nsolves
+    mflops = s1["model_flops"] - s0["model_flops"]
+    mbytes = s1["model_bytes"] - s0["model_bytes"]
+    launches = s1["launches"] - s0["launches"]
+    # ---- plain FP64 cold start and the previous-solution baseline on the same trajectory ----
+    base = {}
+    for guess in ("cold", "previous"):
+        Q = make(guess)
+        run_steps(sw, torch, Q, 2)
+        torch.cuda.synchronize()
+        q0 = sw.get_stats(Q.handle)
+        ev = []
+        run_steps(sw, torch, Q, args.plain_steps, flush=flush, events=ev)
+        torch.cuda.synchronize()
+        q1 = sw.get_stats(Q.handle)
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        n = 5 * args.plain_steps
+        base[guess] = {"value": n / (ms / 1e3), "iters_per_solve": (q1["total_iterations"] - q0["total_iterations"]) / n,
+                       "ms_per_solve": ms / n, "steps": args.plain_steps}
+        Q.close()
+    # ---- end to end through the host-buffer C-ABI call ----
+    e2e = None
+    if not args.no_e2e:
+        R = make("ewma")
+        m, ncol = R.m, R.ncol
+        nrec = args.warmup + args.steps
+        rec_ep = torch.empty((nrec * 5, ncol), dtype=torch.float64, pin_memory=True)
+        rec_ec = torch.empty_like(rec_ep)
+        rec_b = torch.empty((nrec * 5, m), dtype=torch.float64, pin_memory=True)
+        dep = torch.empty(ncol, dtype=torch.float64, device=dev)
+        dec = torch.empty_like(dep)
+        db = torch.empty(m, dtype=torch.float64, device=dev)
+        for q in range(nrec * 5):
+            sw.advance_stage(R.handle)
+            sw.get_last_system(R.handle, dep, dec, db)
+            rec_ep[q].copy_(dep)
+            rec_ec[q].copy_(dec)
+            rec_b[q].copy_(db)
+        torch.cuda.synchronize()
+        R.close()
+        E = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **solver_kw(args, "ewma"))
+        xh = torch.empty(m, dtype=torch.float64, pin_memory=True)
+        for q in range(args.warmup * 5):
+            sw.solve_poisson_host(E.handle, rec_ep[q], rec_ec[q], rec_b[q], xh)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q in range(args.warmup * 5, nrec * 5):
+            sw.solve_poisson_host(E.handle, rec_ep[q], rec_ec[q], rec_b[q], xh)
+        e2e_s = time.perf_counter() - t0
+        E.close()
+        if dist:
+            tt = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * nsolves / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": 5 * (2 * ncol + m) * 8, "d2h_bytes_per_step": 5 * m * 8,
+               "note": "sw_solve_poisson_host on the recorded systems of the same trajectory"}
+    if rank != 0:
+        return
+    peaks = load_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    # FP64 peak from unit counts and clock: 2 FP64 FMA per clock per SM (GB300), 2 flops each
+    fp64_peak = sm_count * 2 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+    achieved_tf = mflops / (solve_ms / 1e3) / 1e12 if solve_ms > 0 else None
+    achieved_gbs = mbytes / (solve_ms / 1e3) / 1e9 if solve_ms > 0 else None
+    traffic = profile_traffic("solve_kernel")
+    roof = {"kernel": "solve_kernel", "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
+            "unit": "TFLOP/s", "frac": (achieved_tf / fp64_peak) if achieved_tf else None,
+            "traffic": traffic, "peak_source": "FP64 2 FMA/clk/SM x %d SMs x %.0f MHz" % (sm_count, peaks.get("sm_max_mhz", 2070.0)),
+            "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": peaks.get("hbm_gbs"),
+                    "frac": (achieved_gbs / peaks["hbm_gbs"]) if achieved_gbs and peaks.get("hbm_gbs") else None},
+            "kernel_ms_per_launch": solve_ms / max(n_timed, 1), "launches_timed": n_timed,
+            "kernel_share_of_step": solve_ms / total_ms if total_ms else None}
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, cits, n, dt = oracle_run(args, 6, 40, budget_s=20.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "iters_per_solve": cits,
+               "sample": "%d EWMA solves of the same workload after 6 warm-up steps, serial FP64 C oracle (%.1f s)"
+                         % (n, dt)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "iters_per_solve": its, "us_per_solve": 1e3 * total_ms / nsolves,
+            "plain": base["cold"], "previous": base["previous"],
+            "speedup_vs_plain": value / base["cold"]["value"] / world,
+            "config": {"workload": WORKLOAD, "nx": 512, "nz": 17, "unknowns": wl["m"], "guess": "ewma", "k": args.k,
+                       "decay": args.decay, "tol": 1e-8, "restart": 20, "n_init_steps": 6, "dt": wl["dt"],
+                       "l2": "flushed between timed steps (256 MiB write, outside the step events)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": launches, "launches_per_solve": launches / nsolves, "wall_s_timed": wall}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    gpu_arm(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -83,6 +83,10 @@ typedef struct {
     double guess_res;      /* ||b - A x0|| / ||b|| */
     long long n_solves;    /* solves since creation */
     long long total_iterations;
+    long long launches;    /* CUDA kernels this library launched since creation */
+    double model_flops;    /* algorithmic FP operations of all solves so far (cost model of the
+                              operator, preconditioner, Gram-Schmidt and guess; not counters) */
+    double model_bytes;    /* algorithmic bytes moved by all solves so far (same model) */
 } sw_stats;
 
 typedef struct {
@@ -159,6 +163,15 @@ int sw_get_state(sw_problem *p, double *d_u, double *d_v, double *d_w, double *d
 /* One stage i (cycling 1..5) of Algorithm 1: K_eta and eta^(i), the right-hand
  * side of Eq. (16)-(17), the Poisson solve, K_u and u^(i). */
 int sw_advance_stage(sw_problem *p, void *stream);
+/* The system A(eta_prev, eta_cur) p = b of the last stage (copies; any pointer may be NULL). */
+int sw_get_last_system(sw_problem *p, double *d_eta_prev, double *d_eta_cur, double *d_b, void *stream);
+
+/* Per-launch timing of the solve kernel with CUDA events recorded on the
+ * launching stream around each solve (off by default).  sw_get_solve_time
+ * synchronises and returns the summed duration in milliseconds and the number
+ * of timed solves since timing was switched on. */
+int sw_enable_timing(sw_problem *p, int on);
+int sw_get_solve_time(sw_problem *p, double *total_ms, long long *n_timed);
 
 /* Last error message of the calling thread (static storage). */
 const char *sw_last_error(void);

@@ -14,7 +14,8 @@ from . import build as _build
 __all__ = ["Grid", "Params", "Stats", "Physics", "Problem", "create_problem", "destroy_problem", "problem_size",
            "solve_poisson", "solve_poisson_host", "get_stats", "apply_operator", "apply_preconditioner",
            "subspace_guess", "get_sketch", "set_sketch", "draw_omega", "set_physics", "set_state", "get_state",
-           "advance_stage", "library_path", "SawaveError", "GUESS", "PRECISION"]
+           "advance_stage", "get_last_system", "enable_timing", "get_solve_time", "library_path", "SawaveError", "GUESS",
+           "PRECISION"]
 
 SW_OK = 0
 STATUS = {0: "OK", -1: "BAD_ARG", -2: "CUDA_ERR", -3: "NOT_CONVERGED", -4: "SINGULAR_PRECOND", -5: "NAN"}
@@ -41,7 +42,8 @@ class Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int), ("status", C.c_int),
                 ("res0", C.c_double), ("res_final", C.c_double), ("true_res", C.c_double),
-                ("guess_res", C.c_double), ("n_solves", C.c_longlong), ("total_iterations", C.c_longlong)]
+                ("guess_res", C.c_double), ("n_solves", C.c_longlong), ("total_iterations", C.c_longlong),
+                ("launches", C.c_longlong), ("model_flops", C.c_double), ("model_bytes", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -84,11 +86,15 @@ def lib():
         L.sw_set_state.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sw_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.sw_advance_stage.argtypes = [vp, vp]
+        L.sw_enable_timing.argtypes = [vp, ip]
+        L.sw_get_last_system.argtypes = [vp, vp, vp, vp, vp]
+        L.sw_get_solve_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
         L.sw_last_error.restype = C.c_char_p
         for name in ["sw_create_problem", "sw_destroy_problem", "sw_problem_size", "sw_solve_poisson",
                      "sw_solve_poisson_host", "sw_get_stats", "sw_apply_operator", "sw_apply_preconditioner",
                      "sw_subspace_guess", "sw_get_sketch", "sw_set_sketch", "sw_draw_omega", "sw_set_physics",
-                     "sw_set_state", "sw_get_state", "sw_advance_stage"]:
+                     "sw_set_state", "sw_get_state", "sw_advance_stage", "sw_enable_timing", "sw_get_solve_time",
+                     "sw_get_last_system"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -210,6 +216,20 @@ def get_state(p, u=None, v=None, w=None, eta=None, pres=None, stream=None):
 
 def advance_stage(p, stream=None):
     return _check(lib().sw_advance_stage(p, _stream(stream)))
+
+
+def get_last_system(p, eta_prev=None, eta_cur=None, b=None, stream=None):
+    return _check(lib().sw_get_last_system(p, _dptr(eta_prev), _dptr(eta_cur), _dptr(b), _stream(stream)))
+
+
+def enable_timing(p, on=True):
+    return _check(lib().sw_enable_timing(p, 1 if on else 0))
+
+
+def get_solve_time(p):
+    ms, n = C.c_double(), C.c_longlong()
+    _check(lib().sw_get_solve_time(p, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
 
 
 class Problem:

@@ -11,6 +11,7 @@
 //   the Poisson solve A(eta^(i-1), eta^(i)) p = b (Algorithm 2);
 //   f_u (Eq. 14a) with grad^(i-1), K_u <- alpha_i K_u + dt f_u, u^(i) = u + beta_i K_u.
 #include <cstring>
+#include <utility>
 
 #include "sw_device.cuh"
 
@@ -272,10 +273,25 @@ extern "C" int sw_advance_stage(sw_problem *pp, void *stream) {
     // the solve recomputed the same geometry pair; f_u uses its stage i-1 half
     fu_kernel<<<gm, T, 0, s>>>(D, P->d_u, P->d_v, P->d_w, P->d_p, P->d_feta, P->d_Ku, P->d_Kv, P->d_Kw, rk);
     update_kernel<<<gm, T, 0, s>>>(D, P->d_u, P->d_v, P->d_w, P->d_Ku, P->d_Kv, P->d_Kw, rk.beta);
-    e = cudaMemcpyAsync(P->d_eta, P->d_eta_new, P->ncol * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "stage launch");
+    // eta^(i) becomes the state; the buffer of eta^(i-1) is kept for sw_get_last_system
+    std::swap(P->d_eta, P->d_eta_new);
+    P->launches += 6;
     P->stage = (P->stage + 1) % 5;
     P->last_stream = s;
+    return SW_OK;
+}
+
+extern "C" int sw_get_last_system(sw_problem *pp, double *ep, double *ec, double *b, void *stream) {
+    Problem *P = (Problem *)pp;
+    if (!P || !P->has_state) { set_error("no state loaded"); return SW_ERR_BAD_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nb = P->ncol * sizeof(double);
+    cudaError_t e = cudaSuccess;
+    if (ep) e = cudaMemcpyAsync(ep, P->d_eta_new, nb, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && ec) e = cudaMemcpyAsync(ec, P->d_eta, nb, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && b) e = cudaMemcpyAsync(b, P->d_rhs, P->m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "get last system");
     return SW_OK;
 }

@@ -430,6 +430,15 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     D.hxx = P->d_hcols + 3 * H.ncol; D.hyy = P->d_hcols + 4 * H.ncol;
     D.gp = P->d_geom;
     D.lu64 = P->d_lu64; D.lu32 = P->d_lu32; D.udinv64 = P->d_udinv64; D.udinv32 = P->d_udinv32;
+    // algorithmic cost per point: 7-point sums counted as 7 fused multiply-adds (14 flops)
+    {
+        double fA = three_d ? 123.0 : 76.0;
+        double bA = 16.0 + 8.0 * (three_d ? 18.0 : 12.0) / H.P;
+        P->cost.fA = fA;
+        P->cost.bA = bA;
+        P->cost.fM = 2.0 * ns - 1.0;
+        P->cost.bM = (ns + 1.0) * 8.0 + 32.0;
+    }
     rc = setup_solver_launch(P);
     if (rc != SW_OK) { sw_destroy_problem((sw_problem *)P); return rc; }
     ALLOC(P->d_part, (size_t)P->nblocks * 2 * 160 * sizeof(double) + 8192);
@@ -442,6 +451,7 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
 extern "C" int sw_destroy_problem(sw_problem *pp) {
     Problem *P = (Problem *)pp;
     if (!P) return SW_OK;
+    for (auto ev : P->ev) cudaEventDestroy(ev);
     for (void *a : P->allocs) cudaFree(a);
     delete P;
     return SW_OK;

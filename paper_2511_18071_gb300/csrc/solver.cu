@@ -25,6 +25,7 @@ struct SolveArgs {
     int guess_only;   // stop after writing x0 (sw_subspace_guess)
     double tol, decay;
     double omega[MAX_K];
+    CostModel cm;
 };
 
 // ---- shared-memory layout of the solve kernel ----
@@ -192,6 +193,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
         return p;
     };
     double *finals = A.part + (size_t)2 * PART_STRIDE * nb;   // PART_STRIDE values
+    // algorithmic cost of this solve (per grid point unit costs times m)
+    double mf = 0.0, mb = 0.0;
+    const double md = (double)m;
+    auto cost = [&](double f, double b) { mf += f * md; mb += b * md; };
     if (threadIdx.x == 0) {
         int e = 0;
         for (int a = 0; a < k; ++a)
@@ -217,12 +222,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
     }
     const double braw = sqrt(S.res[0]);
     const double bnorm = sqrt(S.res[1]);
+    cost(A.cm.fM + 4.0, A.cm.bM + 8.0);
 
     // ---- a7-a10: initial guess (Algorithm 2) ----
     int guess_rank = -1, shifted = 0;
     if (A.pending || A.guess_mode == SW_GUESS_EWMA) {
         // Y_new = r Y_old + x_prev omega^T (Algorithm 4) and W = A Y_new
         const bool upd = A.pending != 0;
+        if (upd) cost(3.0 * k, (2.0 * k + 1.0) * 8.0);
+        if (A.guess_mode == SW_GUESS_EWMA) cost(k * A.cm.fA, k * (A.cm.bA + 8.0));
         for (int c = 0; c < k; ++c) {
             const double *Yc = A.Yold + (size_t)c * m;
             double *Ync = A.Ynew + (size_t)c * m;
@@ -246,6 +254,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
         // Gram G = W^T W and c = W^T b (a8), k(k+1)/2 + k values in chunks of 32
         const int ng = k * (k + 1) / 2;
         const int nv = ng + k;
+        cost(2.0 * nv, (k + 1.0) * 8.0);
         double *pt = part();
         for (int c0 = 0; c0 < nv; c0 += 32) {
             double v[32];
@@ -299,6 +308,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
         __syncthreads();
         const bool ok1 = S.flags[0] != 0;
         if (ok1) {
+            cost((double)k * k + 2.0 * nv, (k + 1.0) * 8.0);
             // second pass: Q1 = W R1^-1, G2 = Q1^T Q1, c2 = Q1^T b
             double *pt2 = part();
             for (int c0 = 0; c0 < nv; c0 += 32) {
@@ -373,12 +383,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
             guess_rank = 0;
         }
         // a10: x0 = Y z
+        cost(2.0 * k, (k + 1.0) * 8.0);
         for (long long p = gtid; p < m; p += gnth) {
             double s = 0.0;
             for (int c = 0; c < k; ++c) s += Ycur[(size_t)c * m + p] * S.z[c];
             A.x[p] = s;
         }
     } else if (A.guess_mode == SW_GUESS_PREVIOUS) {
+        cost(0.0, 16.0);
         for (long long p = gtid; p < m; p += gnth) A.x[p] = A.xprev[p];
     } else {
         for (long long p = gtid; p < m; p += gnth) A.x[p] = 0.0;
@@ -417,6 +429,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
                 grid_sum32(grid, v, 2, S, part(), nb, S.res);
             }
             const double beta = sqrt(S.res[1]);
+            cost(A.cm.fA + A.cm.fM + 4.0, A.cm.bA + A.cm.bM + 8.0);
             if (cycle == 0) {
                 res0 = beta / bnorm;
                 guess_res = braw > 0.0 ? sqrt(S.res[0]) / braw : sqrt(S.res[0]);
@@ -523,6 +536,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
                     S.flags[2] = (fabs(S.g[j + 1]) <= A.tol * bnorm) || hn == 0.0;
                 }
                 __syncthreads();
+                cost(A.cm.fA + A.cm.fM + 8.0 * (j + 1) + 2.0, A.cm.bA + A.cm.bM + (3.0 * j + 8.0) * 8.0);
                 ++iters;
                 jend = j + 1;
                 if (S.flags[2]) break;
@@ -538,6 +552,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
                 }
             }
             __syncthreads();
+            cost(2.0 * jend, (jend + 2.0) * 8.0);
             for (long long p = gtid; p < m; p += gnth) {
                 double s = A.x[p];
                 for (int i = 0; i < jend; ++i) s += S.y[i] * A.V[(size_t)i * m + p];
@@ -559,6 +574,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
         for (long long p = gtid; p < m; p += gnth) A.xprev[p] = A.x[p];
         grid_sum32(grid, v, 1, S, part(), nb, S.res);
         true_res = braw > 0.0 ? sqrt(S.res[0]) / braw : sqrt(S.res[0]);
+        cost(A.cm.fA + 3.0, A.cm.bA + 24.0);
     }
     if (gtid == 0) {
         DevStats &st = *A.stats;
@@ -576,6 +592,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
         st.guess_mode = A.guess_mode;
         st.cholesky_shift = shifted;
         st.total_iterations += iters;
+        st.model_flops += mf;
+        st.model_bytes += mb;
     }
 }
 
@@ -676,6 +694,21 @@ int setup_solver_launch(Problem *P) {
 
 static Tiling tiling_of(const Problem *P) { return make_tiling(P->dev); }
 
+// Fold the recorded event pairs into the running total.
+static int flush_timing(Problem *P) {
+    for (int i = 0; i < P->ev_used; ++i) {
+        cudaError_t e = cudaEventSynchronize(P->ev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "event sync");
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, P->ev[2 * i], P->ev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "event time");
+        P->timed_ms += ms;
+        P->n_timed++;
+    }
+    P->ev_used = 0;
+    return SW_OK;
+}
+
 static int launch_solve(Problem *P, const double *ep, const double *ec, const double *b, double *x,
                         cudaStream_t s, int guess_only) {
     const sw_params &pr = P->params;
@@ -691,12 +724,29 @@ static int launch_solve(Problem *P, const double *ep, const double *ec, const do
     if (mode == SW_GUESS_EWMA && P->n_solves < pr.n_init_solves) mode = SW_GUESS_PREVIOUS;
     if (guess_only) mode = SW_GUESS_EWMA;
     A.guess_mode = mode;
+    A.cm = P->cost;
     A.pending = P->pending ? 1 : 0;
     if (A.pending) sw_draw_omega(pr.seed, P->n_solves - 1, pr.k, A.omega);
     Dev D = P->dev;
     void *args[] = {&D, &A};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)solve_kernel, P->nblocks, NTHREADS, args, P->smem, s);
+    cudaError_t e = cudaSuccess;
+    int evi = -1;
+    if (P->timing) {
+        if (P->ev_used * 2 + 2 > (int)P->ev.size()) {
+            int rc = flush_timing(P);
+            if (rc != SW_OK) return rc;
+        }
+        evi = P->ev_used++;
+        e = cudaEventRecord(P->ev[2 * evi], s);
+        if (e != cudaSuccess) return cuda_fail(e, "event record");
+    }
+    e = cudaLaunchCooperativeKernel((const void *)solve_kernel, P->nblocks, NTHREADS, args, P->smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+    P->launches++;
+    if (evi >= 0) {
+        e = cudaEventRecord(P->ev[2 * evi + 1], s);
+        if (e != cudaSuccess) return cuda_fail(e, "event record");
+    }
     if (A.pending) P->ybuf ^= 1;
     P->pending = false;
     if (!guess_only) {
@@ -769,6 +819,40 @@ extern "C" int sw_get_stats(sw_problem *pp, sw_stats *out) {
     out->guess_res = st.guess_res;
     out->n_solves = P->n_solves;
     out->total_iterations = st.total_iterations;
+    out->launches = P->launches;
+    out->model_flops = st.model_flops;
+    out->model_bytes = st.model_bytes;
+    return SW_OK;
+}
+
+extern "C" int sw_enable_timing(sw_problem *pp, int on) {
+    Problem *P = (Problem *)pp;
+    if (!P) { set_error("null argument"); return SW_ERR_BAD_ARG; }
+    if (on && P->ev.empty()) {
+        P->ev.resize(512);
+        for (auto &ev : P->ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return cuda_fail(e, "event create");
+        }
+    }
+    if (P->timing && !on) {
+        int rc = flush_timing(P);
+        if (rc != SW_OK) return rc;
+    }
+    P->timing = on != 0;
+    P->timed_ms = 0.0;
+    P->n_timed = 0;
+    P->ev_used = 0;
+    return SW_OK;
+}
+
+extern "C" int sw_get_solve_time(sw_problem *pp, double *total_ms, long long *n_timed) {
+    Problem *P = (Problem *)pp;
+    if (!P || !total_ms || !n_timed) { set_error("null argument"); return SW_ERR_BAD_ARG; }
+    int rc = flush_timing(P);
+    if (rc != SW_OK) return rc;
+    *total_ms = P->timed_ms;
+    *n_timed = P->n_timed;
     return SW_OK;
 }
 
@@ -783,6 +867,7 @@ extern "C" int sw_apply_operator(sw_problem *pp, const double *ep, const double 
     apply_kernel<<<tl.ntiles, NTHREADS, 2 * (size_t)P->dev.P * tl.HW * sizeof(double), s>>>(P->dev, tl, x, y);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "apply launch");
+    P->launches += 2;
     P->last_stream = s;
     return SW_OK;
 }
@@ -797,6 +882,7 @@ extern "C" int sw_apply_preconditioner(sw_problem *pp, const double *v, double *
     for (int c = 3; c >= 0; --c) ilu_bwd_kernel<<<blocks, NTHREADS, 0, s>>>(P->dev, c, out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "preconditioner launch");
+    P->launches += 8;
     P->last_stream = s;
     return SW_OK;
 }
@@ -825,6 +911,7 @@ extern "C" int sw_get_sketch(sw_problem *pp, double *Y, void *stream) {
         sketch_update_kernel<<<blocks, NTHREADS, 0, s>>>(Y, P->d_xprev, u, P->params.k, P->m, P->params.decay);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "sketch update launch");
+        P->launches++;
     }
     P->last_stream = s;
     return SW_OK;

@@ -47,6 +47,12 @@ struct Dev {
     const float *udinv32;
 };
 
+// Algorithmic cost per grid point of the building blocks (FP64 words).
+struct CostModel {
+    double fA, bA;   // operator apply
+    double fM, bM;   // preconditioner application
+};
+
 struct Problem {
     sw_grid grid;
     sw_params params;
@@ -88,6 +94,14 @@ struct Problem {
     size_t smem = 0;
     cudaStream_t last_stream = nullptr;
     bool has_state = false;
+    long long launches = 0;        // kernels launched by this problem
+    CostModel cost{};
+    // solve-kernel timing (events on the launching stream)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;   // pairs (start, stop)
+    int ev_used = 0;
+    double timed_ms = 0.0;
+    long long n_timed = 0;
 };
 
 // Statistics written by the device at the end of a solve.
@@ -96,7 +110,9 @@ struct DevStats {
     double res0, res_final, true_res, guess_res, bnorm, braw;
     int guess_rank, guess_mode, cholesky_shift, pad;
     long long total_iterations;
+    double model_flops, model_bytes;
 };
+
 
 void set_error(const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
