@@ -166,6 +166,22 @@ int sw_advance_stage(sw_problem *p, void *stream);
 /* The system A(eta_prev, eta_cur) p = b of the last stage (copies; any pointer may be NULL). */
 int sw_get_last_system(sw_problem *p, double *d_eta_prev, double *d_eta_cur, double *d_b, void *stream);
 
+/* Allocation-free operator apply: y = A(eta_prev, eta_cur) x as in
+ * sw_apply_operator, but without a problem handle and without allocating
+ * device memory.  The paper has no counterpart; this exists for callers that
+ * cannot call cudaMalloc (a memory budget or pool that forbids new device
+ * allocations, or a framework that hands over only its own buffers).
+ * All pointers except `grid` are device pointers owned by the caller: d_h
+ * (nx*ny depths), d_eta_prev and d_eta_cur (nx*ny), d_x and d_y (m each).
+ * Scratch lives in one static device array sized for at most 65,536 columns
+ * (nx*ny; about 12.6 MB held by every GPU that loads the library until exit);
+ * larger grids return SW_ERR_BAD_ARG.  The first call on a device resolves
+ * the array's address and should come before any stream capture.  Calls share
+ * the array: two calls that overlap on the GPU race.  Same grid rules as
+ * sw_create_problem. */
+int sw_apply_operator_noalloc(const sw_grid *grid, const double *d_h, const double *d_eta_prev,
+                              const double *d_eta_cur, const double *d_x, double *d_y, void *stream);
+
 /* Per-launch timing of the solve kernel with CUDA events recorded on the
  * launching stream around each solve (off by default).  sw_get_solve_time
  * synchronises and returns the summed duration in milliseconds and the number

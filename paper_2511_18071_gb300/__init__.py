@@ -13,7 +13,7 @@ from . import build as _build
 
 __all__ = ["Grid", "Params", "Stats", "Physics", "Problem", "create_problem", "destroy_problem", "problem_size",
            "solve_poisson", "solve_poisson_host", "get_stats", "apply_operator", "apply_preconditioner",
-           "subspace_guess", "get_sketch", "set_sketch", "draw_omega", "set_physics", "set_state", "get_state",
+           "subspace_guess", "apply_operator_noalloc", "get_sketch", "set_sketch", "draw_omega", "set_physics", "set_state", "get_state",
            "advance_stage", "get_last_system", "enable_timing", "get_solve_time", "library_path", "SawaveError", "GUESS",
            "PRECISION"]
 
@@ -88,13 +88,14 @@ def lib():
         L.sw_advance_stage.argtypes = [vp, vp]
         L.sw_enable_timing.argtypes = [vp, ip]
         L.sw_get_last_system.argtypes = [vp, vp, vp, vp, vp]
+        L.sw_apply_operator_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp, vp, vp, vp]
         L.sw_get_solve_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
         L.sw_last_error.restype = C.c_char_p
         for name in ["sw_create_problem", "sw_destroy_problem", "sw_problem_size", "sw_solve_poisson",
                      "sw_solve_poisson_host", "sw_get_stats", "sw_apply_operator", "sw_apply_preconditioner",
                      "sw_subspace_guess", "sw_get_sketch", "sw_set_sketch", "sw_draw_omega", "sw_set_physics",
                      "sw_set_state", "sw_get_state", "sw_advance_stage", "sw_enable_timing", "sw_get_solve_time",
-                     "sw_get_last_system"]:
+                     "sw_get_last_system", "sw_apply_operator_noalloc"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -181,6 +182,12 @@ def apply_operator(p, eta_prev, eta_cur, x, y, stream=None):
 
 def apply_preconditioner(p, v, out, stream=None):
     return _check(lib().sw_apply_preconditioner(p, _dptr(v), _dptr(out), _stream(stream)))
+
+
+def apply_operator_noalloc(grid, h, eta_prev, eta_cur, x, y, stream=None):
+    """Operator apply that allocates no device memory (scratch in a static device array)."""
+    return _check(lib().sw_apply_operator_noalloc(C.byref(grid), _dptr(h), _dptr(eta_prev), _dptr(eta_cur), _dptr(x),
+                                                  _dptr(y), _stream(stream)))
 
 
 def subspace_guess(p, eta_prev, eta_cur, b, x0, stream=None):
