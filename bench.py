@@ -230,6 +230,7 @@ def gpu_arm(args, rank, world, local_rank):
     run_steps(sw, torch, P, args.warmup)
     torch.cuda.synchronize()
     s0 = sw.get_stats(P.handle)
+    ph0 = sw.get_phase_times(P.handle)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -250,6 +251,7 @@ def gpu_arm(args, rank, world, local_rank):
     solve_ms, n_timed = sw.get_solve_time(P.handle)
     sw.enable_timing(P.handle, False)
     s1 = sw.get_stats(P.handle)
+    ph1 = sw.get_phase_times(P.handle)
     nsolves = 5 * args.steps
     if dist:
         tt = torch.tensor([total_ms], device=dev)
@@ -267,14 +269,18 @@ def gpu_arm(args, rank, world, local_rank):
         run_steps(sw, torch, Q, 2)
         torch.cuda.synchronize()
         q0 = sw.get_stats(Q.handle)
+        qp0 = sw.get_phase_times(Q.handle)
         ev = []
         run_steps(sw, torch, Q, args.plain_steps, flush=flush, events=ev)
         torch.cuda.synchronize()
         q1 = sw.get_stats(Q.handle)
+        qp1 = sw.get_phase_times(Q.handle)
         ms = sum(a.elapsed_time(b) for a, b in ev)
         n = 5 * args.plain_steps
-        base[guess] = {"value": n / (ms / 1e3), "iters_per_solve": (q1["total_iterations"] - q0["total_iterations"]) / n,
-                       "ms_per_solve": ms / n, "steps": args.plain_steps}
+        nit = q1["total_iterations"] - q0["total_iterations"]
+        base[guess] = {"value": n / (ms / 1e3), "iters_per_solve": nit / n,
+                       "ms_per_solve": ms / n, "steps": args.plain_steps,
+                       "phase_us_per_iteration": {k: round((qp1[k] - qp0[k]) / max(nit, 1), 2) for k in qp1}}
         Q.close()
     # ---- end to end through the host-buffer C-ABI call ----
     e2e = None
@@ -346,7 +352,8 @@ def gpu_arm(args, rank, world, local_rank):
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-            "gpu_launches": launches, "launches_per_solve": launches / nsolves, "wall_s_timed": wall}
+            "gpu_launches": launches, "launches_per_solve": launches / nsolves, "wall_s_timed": wall,
+            "phase_us_per_solve": {k: round((ph1[k] - ph0[k]) / nsolves, 2) for k in ph1}}
     print(json.dumps(line), flush=True)
 
 

@@ -189,6 +189,14 @@ int sw_apply_operator_noalloc(const sw_grid *grid, const double *d_h, const doub
 int sw_enable_timing(sw_problem *p, int on);
 int sw_get_solve_time(sw_problem *p, double *total_ms, long long *n_timed);
 
+/* Profiling aid: cumulative device time in microseconds spent in each phase of
+ * all solves so far, as seen by one thread between grid barriers (n <= 16
+ * values): 0 geometry, 1 ||M^-1 b||, 2 sketch update and W = A Y, 3 Gram and
+ * least squares, 4 residual apply, 5 residual preconditioner and norm,
+ * 6 Arnoldi apply, 7 Arnoldi preconditioner, 8-10 the three Gram-Schmidt
+ * passes, 11 Givens rotations, 12 solution update, 13 true residual. */
+int sw_get_phase_times(sw_problem *p, double *us, int n);
+
 /* Last error message of the calling thread (static storage). */
 const char *sw_last_error(void);
 

@@ -14,7 +14,7 @@ from . import build as _build
 __all__ = ["Grid", "Params", "Stats", "Physics", "Problem", "create_problem", "destroy_problem", "problem_size",
            "solve_poisson", "solve_poisson_host", "get_stats", "apply_operator", "apply_preconditioner",
            "subspace_guess", "apply_operator_noalloc", "get_sketch", "set_sketch", "draw_omega", "set_physics", "set_state", "get_state",
-           "advance_stage", "get_last_system", "enable_timing", "get_solve_time", "library_path", "SawaveError", "GUESS",
+           "advance_stage", "get_last_system", "get_phase_times", "enable_timing", "get_solve_time", "library_path", "SawaveError", "GUESS",
            "PRECISION"]
 
 SW_OK = 0
@@ -89,13 +89,14 @@ def lib():
         L.sw_enable_timing.argtypes = [vp, ip]
         L.sw_get_last_system.argtypes = [vp, vp, vp, vp, vp]
         L.sw_apply_operator_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp, vp, vp, vp]
+        L.sw_get_phase_times.argtypes = [vp, vp, ip]
         L.sw_get_solve_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
         L.sw_last_error.restype = C.c_char_p
         for name in ["sw_create_problem", "sw_destroy_problem", "sw_problem_size", "sw_solve_poisson",
                      "sw_solve_poisson_host", "sw_get_stats", "sw_apply_operator", "sw_apply_preconditioner",
                      "sw_subspace_guess", "sw_get_sketch", "sw_set_sketch", "sw_draw_omega", "sw_set_physics",
                      "sw_set_state", "sw_get_state", "sw_advance_stage", "sw_enable_timing", "sw_get_solve_time",
-                     "sw_get_last_system", "sw_apply_operator_noalloc"]:
+                     "sw_get_last_system", "sw_apply_operator_noalloc", "sw_get_phase_times"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -227,6 +228,18 @@ def advance_stage(p, stream=None):
 
 def get_last_system(p, eta_prev=None, eta_cur=None, b=None, stream=None):
     return _check(lib().sw_get_last_system(p, _dptr(eta_prev), _dptr(eta_cur), _dptr(b), _stream(stream)))
+
+
+PHASES = ["geometry", "bnorm", "guess_w", "guess_ls", "res_apply", "res_ilu", "arn_apply", "arn_ilu", "cgs1", "cgs2",
+          "cgs3", "givens", "update", "true_res"]
+
+
+def get_phase_times(p):
+    """Cumulative device microseconds per solve phase (profiling aid)."""
+    import numpy as np
+    out = np.zeros(16)
+    _check(lib().sw_get_phase_times(p, C.c_void_p(out.ctypes.data), 16))
+    return dict(zip(PHASES, out[:len(PHASES)].tolist()))
 
 
 def enable_timing(p, on=True):

@@ -354,6 +354,53 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     std::vector<double> lu_rows, udinv;
     int st = factorise(H, lu_rows, udinv);
     if (st != SW_OK) { set_error("zero pivot in ILU(0)"); return st; }
+    // In-column blocks: rows of one column are consecutive ranks, so the
+    // column's part of L (unit lower) and U (upper) are P x P blocks; their
+    // inverses turn the in-column recurrences into small dense products.
+    std::vector<double> linv((size_t)H.ncol * H.P * H.P, 0.0), uinv((size_t)H.ncol * H.P * H.P, 0.0);
+    {
+        const int Pl = H.P, ns = H.nslot;
+        std::vector<double> Lb(Pl * Pl), Ub(Pl * Pl), X(Pl * Pl);
+        for (long long cr = 0; cr < H.ncol; ++cr) {
+            std::fill(Lb.begin(), Lb.end(), 0.0);
+            std::fill(Ub.begin(), Ub.end(), 0.0);
+            for (int a = 0; a < Pl; ++a) {
+                int j = a - 1;
+                long long r = cr * Pl + a;
+                int w0 = H.win[j + 1];
+                Lb[a * Pl + a] = 1.0;
+                for (int kk = 0; kk < W; ++kk) {
+                    int lev = w0 + kk, b = lev + 1;
+                    double v = lu_rows[(size_t)r * ns + sigma_slot(H.layout, kk)];
+                    if (!H.in_pattern(sigma_slot(H.layout, kk), j)) continue;
+                    if (b < a) Lb[a * Pl + b] = v;
+                    else Ub[a * Pl + b] = v;
+                }
+            }
+            // L^-1 by forward substitution, column by column
+            std::fill(X.begin(), X.end(), 0.0);
+            for (int c = 0; c < Pl; ++c) {
+                for (int a = 0; a < Pl; ++a) {
+                    double sum = a == c ? 1.0 : 0.0;
+                    for (int b = 0; b < a; ++b) sum -= Lb[a * Pl + b] * X[b * Pl + c];
+                    X[a * Pl + c] = sum;
+                }
+            }
+            for (int a = 0; a < Pl; ++a)
+                for (int c = 0; c < Pl; ++c) linv[((size_t)cr * Pl + c) * Pl + a] = X[a * Pl + c];
+            // U^-1 by backward substitution
+            std::fill(X.begin(), X.end(), 0.0);
+            for (int c = 0; c < Pl; ++c) {
+                for (int a = Pl - 1; a >= 0; --a) {
+                    double sum = a == c ? 1.0 : 0.0;
+                    for (int b = a + 1; b < Pl; ++b) sum -= Ub[a * Pl + b] * X[b * Pl + c];
+                    X[a * Pl + c] = sum / Ub[a * Pl + a];
+                }
+            }
+            for (int a = 0; a < Pl; ++a)
+                for (int c = 0; c < Pl; ++c) uinv[((size_t)cr * Pl + c) * Pl + a] = X[a * Pl + c];
+        }
+    }
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -383,6 +430,10 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     ALLOC(P->d_udinv64, (size_t)m * sizeof(double));
     ALLOC(P->d_lu32, (size_t)m * ns * sizeof(float));
     ALLOC(P->d_udinv32, (size_t)m * sizeof(float));
+    ALLOC(P->d_linv64, linv.size() * sizeof(double));
+    ALLOC(P->d_uinv64, uinv.size() * sizeof(double));
+    ALLOC(P->d_linv32, linv.size() * sizeof(float));
+    ALLOC(P->d_uinv32, uinv.size() * sizeof(float));
     ALLOC(P->d_V, (size_t)(p.restart + 1) * m * sizeof(double));
     if (p.precision == SW_PRECISION_MIXED) ALLOC(P->d_V32, (size_t)(p.restart + 1) * m * sizeof(float));
     ALLOC(P->d_work, 6 * (size_t)m * sizeof(double));
@@ -418,6 +469,13 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
         for (size_t i = 0; i < udinv.size(); ++i) u32[i] = (float)udinv[i];
         if (e == cudaSuccess) e = cudaMemcpy(P->d_udinv64, udinv.data(), m * sizeof(double), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(P->d_udinv32, u32.data(), m * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_linv64, linv.data(), linv.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_uinv64, uinv.data(), uinv.size() * sizeof(double), cudaMemcpyHostToDevice);
+        std::vector<float> f32(linv.size());
+        for (size_t i = 0; i < linv.size(); ++i) f32[i] = (float)linv[i];
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_linv32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice);
+        for (size_t i = 0; i < uinv.size(); ++i) f32[i] = (float)uinv[i];
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_uinv32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) { sw_destroy_problem((sw_problem *)P); return cuda_fail(e, "upload"); }
     Dev &D = P->dev;
@@ -430,6 +488,7 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     D.hxx = P->d_hcols + 3 * H.ncol; D.hyy = P->d_hcols + 4 * H.ncol;
     D.gp = P->d_geom;
     D.lu64 = P->d_lu64; D.lu32 = P->d_lu32; D.udinv64 = P->d_udinv64; D.udinv32 = P->d_udinv32;
+    D.linv64 = P->d_linv64; D.uinv64 = P->d_uinv64; D.linv32 = P->d_linv32; D.uinv32 = P->d_uinv32;
     // algorithmic cost per point: 7-point sums counted as 7 fused multiply-adds (14 flops)
     {
         double fA = three_d ? 123.0 : 76.0;

@@ -28,6 +28,18 @@ struct SolveArgs {
     CostModel cm;
 };
 
+// Phases of a solve, timed by block 0 between grid barriers (profiling aid).
+enum Phase {
+    PH_GEOM = 0, PH_BNORM, PH_GUESS_W, PH_GUESS_LS, PH_RES_APPLY, PH_RES_ILU, PH_ARN_APPLY, PH_ARN_ILU,
+    PH_CGS1, PH_CGS2, PH_CGS3, PH_GIVENS, PH_UPDATE, PH_TRUERES, PH_COUNT
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
 // ---- shared-memory layout of the solve kernel ----
 struct SmemFixed {
     double red[NWARPS * 32];
@@ -35,6 +47,7 @@ struct SmemFixed {
     double H[(MAX_RESTART + 1) * MAX_RESTART];
     double cs[MAX_RESTART], sn[MAX_RESTART], g[MAX_RESTART + 1], y[MAX_RESTART];
     double scale[MAX_RESTART + 1];
+    double hs[MAX_RESTART];        // projection coefficients of the current Gram-Schmidt pass, times scale
     double G[MAX_K * MAX_K], R1[MAX_K * MAX_K], R2[MAX_K * MAX_K], R[MAX_K * MAX_K];
     double c1[MAX_K], c2[MAX_K], z[MAX_K], tmp[MAX_K];
     int flags[8];
@@ -91,10 +104,10 @@ __device__ inline void ilu_apply_grid(const Dev &D, cg::grid_group &grid, const 
 
 // Sum n <= 32 per-thread values over the grid into out[] (shared, all blocks).
 __device__ inline void grid_sum32(cg::grid_group &grid, double (&v)[32], int n, SmemFixed &S, double *part, int nb,
-                                  double *out) {
-    block_partials32(v, n, S.red, part, nb);
+                                  double *out, bool active = true) {
+    block_partials32(v, n, S.red, part, nb, active);
     grid.sync();
-    gather_partials(part, n, nb, out);
+    gather_partials(part, n, nb, out, S.red);
 }
 
 // Distributed variant for many values: block b finishes values b, b + nb, ...
@@ -103,8 +116,10 @@ __device__ inline void grid_sum_many(cg::grid_group &grid, const double *part, i
                                      double *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = blockIdx.x * NWARPS + warp; i < n; i += nb * NWARPS) {
-        double s = 0.0;
-        for (int b = lane; b < nb; b += 32) s += part[i * nb + b];
+        double t[5];
+#pragma unroll
+        for (int u = 0; u < 5; ++u) t[u] = lane + 32 * u < nb ? part[i * nb + lane + 32 * u] : 0.0;
+        double s = (t[0] + t[1]) + (t[2] + t[3]) + t[4];
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) finals[i] = s;
@@ -197,6 +212,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
     double mf = 0.0, mb = 0.0;
     const double md = (double)m;
     auto cost = [&](double f, double b) { mf += f * md; mb += b * md; };
+    double ph[PH_COUNT];
+    for (int i = 0; i < PH_COUNT; ++i) ph[i] = 0.0;
+    unsigned long long t_last = global_ns();
+    auto tick = [&](int phase) {
+        if (gtid == 0) {
+            unsigned long long t = global_ns();
+            ph[phase] += (double)(t - t_last);
+            t_last = t;
+        }
+    };
     if (threadIdx.x == 0) {
         int e = 0;
         for (int a = 0; a < k; ++a)
@@ -206,6 +231,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
     // a1: geometry of the stage pair
     geometry_columns(D, A.eta_prev, A.eta_cur, gtid, gnth);
     grid.sync();
+    tick(PH_GEOM);
 
     // reference norms ||b|| and ||M^-1 b||
     ilu_apply_grid(D, grid, A.b, A.t);
@@ -223,6 +249,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
     const double braw = sqrt(S.res[0]);
     const double bnorm = sqrt(S.res[1]);
     cost(A.cm.fM + 4.0, A.cm.bM + 8.0);
+    tick(PH_BNORM);
 
     // ---- a7-a10: initial guess (Algorithm 2) ----
     int guess_rank = -1, shifted = 0;
@@ -249,6 +276,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
         }
         grid.sync();
     }
+    tick(PH_GUESS_W);
     const double *Ycur = A.pending ? A.Ynew : A.Yold;
     if (A.guess_mode == SW_GUESS_EWMA) {
         // Gram G = W^T W and c = W^T b (a8), k(k+1)/2 + k values in chunks of 32
@@ -396,6 +424,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
         for (long long p = gtid; p < m; p += gnth) A.x[p] = 0.0;
     }
     grid.sync();
+    tick(PH_GUESS_LS);
     if (A.guess_only) {
         if (gtid == 0) {
             A.stats->guess_rank = guess_rank;
@@ -424,9 +453,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
                 for (int i = 0; i < 32; ++i) v[i] = 0.0;
                 v[0] = st.acc;
                 grid.sync();
+                tick(PH_RES_APPLY);
                 ilu_apply_grid(D, grid, A.r, A.V);
                 for (long long p = gtid; p < m; p += gnth) v[1] += A.V[p] * A.V[p];
                 grid_sum32(grid, v, 2, S, part(), nb, S.res);
+                tick(PH_RES_ILU);
             }
             const double beta = sqrt(S.res[1]);
             cost(A.cm.fA + A.cm.fM + 4.0, A.cm.bA + A.cm.bM + 8.0);
@@ -454,68 +485,93 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
                     StVec st{A.t};
                     apply_grid(D, A.tl, sp, sq, ld, st);
                     grid.sync();
+                    tick(PH_ARN_APPLY);
                     ilu_apply_grid(D, grid, A.t, w);
+                    tick(PH_ARN_ILU);
                 }
                 // CGS2 pass 1: d_i = V_i . w
+                // Gram-Schmidt passes: warp w of block b takes 32-point chunks
+                // b + nb w, b + nb (w + NWARPS), ... so that the warps holding
+                // data are spread over the blocks and sub-partitions
+                const int wlane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+                const long long k0 = blockIdx.x + (long long)nb * wid, kstep = (long long)nb * NWARPS;
+                const bool wactive = 32 * k0 < m;
                 double v[32];
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = 0.0;
-                for (long long p = gtid; p < m; p += gnth) {
-                    double wv = w[p];
+                for (long long kc = k0; 32 * kc < m; kc += kstep) {
+                    const long long p = 32 * kc + wlane;
+                    if (p >= m) continue;
+                    double vb[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) vb[i] = i <= j ? A.V[(size_t)i * m + p] : 0.0;
+                    const double wv = w[p];
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         if (i > j) break;
-                        v[i] += A.V[(size_t)i * m + p] * wv;
+                        v[i] += vb[i] * wv;
                     }
                 }
-                grid_sum32(grid, v, j + 1, S, part(), nb, S.res);
-                double hs[MAX_RESTART];
-#pragma unroll
-                for (int i = 0; i < MAX_RESTART; ++i) {
-                    if (i > j) break;
-                    double hi = S.res[i] * S.scale[i];
-                    if (threadIdx.x == 0) S.H[i * MAX_RESTART + j] = hi;
-                    hs[i] = hi * S.scale[i];
+                grid_sum32(grid, v, j + 1, S, part(), nb, S.res, wactive);
+                tick(PH_CGS1);
+                if (threadIdx.x < MAX_RESTART) {
+                    const int i = threadIdx.x;
+                    double hi = i <= j ? S.res[i] * S.scale[i] : 0.0;
+                    if (i <= j) S.H[i * MAX_RESTART + j] = hi;
+                    S.hs[i] = i <= j ? hi * S.scale[i] : 0.0;
                 }
+                __syncthreads();
                 // pass 2: w -= V h ; d'_i = V_i . w
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = 0.0;
-                for (long long p = gtid; p < m; p += gnth) {
+                for (long long kc = k0; 32 * kc < m; kc += kstep) {
+                    const long long p = 32 * kc + wlane;
+                    if (p >= m) continue;
+                    double vb[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) vb[i] = i <= j ? A.V[(size_t)i * m + p] : 0.0;
                     double wv = w[p];
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         if (i > j) break;
-                        wv -= hs[i] * A.V[(size_t)i * m + p];
+                        wv -= S.hs[i] * vb[i];
                     }
                     w[p] = wv;
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         if (i > j) break;
-                        v[i] += A.V[(size_t)i * m + p] * wv;
+                        v[i] += vb[i] * wv;
                     }
                 }
-                grid_sum32(grid, v, j + 1, S, part(), nb, S.res);
-#pragma unroll
-                for (int i = 0; i < MAX_RESTART; ++i) {
-                    if (i > j) break;
-                    double hi = S.res[i] * S.scale[i];
-                    if (threadIdx.x == 0) S.H[i * MAX_RESTART + j] += hi;
-                    hs[i] = hi * S.scale[i];
+                grid_sum32(grid, v, j + 1, S, part(), nb, S.res, wactive);
+                tick(PH_CGS2);
+                if (threadIdx.x < MAX_RESTART) {
+                    const int i = threadIdx.x;
+                    double hi = i <= j ? S.res[i] * S.scale[i] : 0.0;
+                    if (i <= j) S.H[i * MAX_RESTART + j] += hi;
+                    S.hs[i] = i <= j ? hi * S.scale[i] : 0.0;
                 }
+                __syncthreads();
                 // pass 3: w -= V h' ; ||w||^2
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = 0.0;
-                for (long long p = gtid; p < m; p += gnth) {
+                for (long long kc = k0; 32 * kc < m; kc += kstep) {
+                    const long long p = 32 * kc + wlane;
+                    if (p >= m) continue;
+                    double vb[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) vb[i] = i <= j ? A.V[(size_t)i * m + p] : 0.0;
                     double wv = w[p];
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         if (i > j) break;
-                        wv -= hs[i] * A.V[(size_t)i * m + p];
+                        wv -= S.hs[i] * vb[i];
                     }
                     w[p] = wv;
                     v[0] += wv * wv;
                 }
-                grid_sum32(grid, v, 1, S, part(), nb, S.res);
+                grid_sum32(grid, v, 1, S, part(), nb, S.res, wactive);
+                tick(PH_CGS3);
                 // a5: Hessenberg column, Givens rotations, residual estimate
                 if (threadIdx.x == 0) {
                     double hn = sqrt(S.res[0]);
@@ -536,6 +592,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
                     S.flags[2] = (fabs(S.g[j + 1]) <= A.tol * bnorm) || hn == 0.0;
                 }
                 __syncthreads();
+                tick(PH_GIVENS);
                 cost(A.cm.fA + A.cm.fM + 8.0 * (j + 1) + 2.0, A.cm.bA + A.cm.bM + (3.0 * j + 8.0) * 8.0);
                 ++iters;
                 jend = j + 1;
@@ -559,6 +616,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
                 A.x[p] = s;
             }
             grid.sync();
+            tick(PH_UPDATE);
         }
     }
     // true residual ||b - A x|| / ||b||, solution kept for the next guess
@@ -576,6 +634,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
         true_res = braw > 0.0 ? sqrt(S.res[0]) / braw : sqrt(S.res[0]);
         cost(A.cm.fA + 3.0, A.cm.bA + 24.0);
     }
+    tick(PH_TRUERES);
     if (gtid == 0) {
         DevStats &st = *A.stats;
         st.iterations = iters;
@@ -594,6 +653,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
         st.total_iterations += iters;
         st.model_flops += mf;
         st.model_bytes += mb;
+        for (int i = 0; i < PH_COUNT; ++i) st.phase_ns[i] += ph[i];
     }
 }
 
@@ -686,7 +746,8 @@ int setup_solver_launch(Problem *P) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel, NTHREADS, smem);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy");
     if (per < 1) { set_error("solve kernel does not fit on an SM"); return SW_ERR_BAD_ARG; }
-    P->nblocks = nsm;
+    // one block per SM; the cross-block gathers are sized for at most 160 blocks
+    P->nblocks = nsm < NWARPS * GATHER_PER_WARP ? nsm : NWARPS * GATHER_PER_WARP;
     P->nthreads = NTHREADS;
     P->smem = smem;
     return SW_OK;
@@ -822,6 +883,19 @@ extern "C" int sw_get_stats(sw_problem *pp, sw_stats *out) {
     out->launches = P->launches;
     out->model_flops = st.model_flops;
     out->model_bytes = st.model_bytes;
+    return SW_OK;
+}
+
+extern "C" int sw_get_phase_times(sw_problem *pp, double *us, int n) {
+    Problem *P = (Problem *)pp;
+    if (!P || !us || n < 1) { set_error("bad argument"); return SW_ERR_BAD_ARG; }
+    DevStats st;
+    std::memset(&st, 0, sizeof(st));
+    if (P->n_solves > 0) {
+        int rc = read_stats(P, &st);
+        if (rc != SW_OK) return rc;
+    }
+    for (int i = 0; i < n && i < 16; ++i) us[i] = i < PH_COUNT ? st.phase_ns[i] * 1e-3 : 0.0;
     return SW_OK;
 }
 

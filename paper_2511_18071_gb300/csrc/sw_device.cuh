@@ -269,116 +269,165 @@ __device__ __forceinline__ int colour_of(const Dev &D, int col) {
     return (ix + iy) & 3;
 }
 
-// forward (lower) sweep of one column of colour c; in -> out
-template <typename T, typename TI>
-__device__ inline void ilu_fwd_column(const Dev &D, int c, int q, const TI *in, T *out, int lane) {
-    const T *lu = lu_ptr<T>(D);
+// Off-column slots of each layout, enumerated at compile time: i -> (slot,
+// dx, dy, window offset kk or -1 for "same level").
+template <int L> struct Off;
+template <> struct Off<CROSS2D> {
+    static constexpr int N = 6;
+    __device__ static constexpr int slot(int i) { return i; }
+    __device__ static constexpr int ox(int i) { return i < 3 ? i - 3 : i - 2; }
+    __device__ static constexpr int oy(int) { return 0; }
+    __device__ static constexpr int kk(int) { return -1; }
+};
+template <> struct Off<BOX2D> {
+    static constexpr int N = 42;
+    __device__ static constexpr int ox(int i) { return (i / 7) < 3 ? (i / 7) - 3 : (i / 7) - 2; }
+    __device__ static constexpr int oy(int) { return 0; }
+    __device__ static constexpr int kk(int i) { return i % 7; }
+    __device__ static constexpr int slot(int i) { return (ox(i) + 3) * 7 + i % 7; }
+};
+template <> struct Off<CROSS3D> {
+    static constexpr int N = 12;
+    __device__ static constexpr int slot(int i) { return i; }
+    __device__ static constexpr int ox(int i) { return i < 6 ? (i < 3 ? i - 3 : i - 2) : 0; }
+    __device__ static constexpr int oy(int i) { return i < 6 ? 0 : ((i - 6) < 3 ? (i - 6) - 3 : (i - 6) - 2); }
+    __device__ static constexpr int kk(int) { return -1; }
+};
+template <> struct Off<BOX3D> {
+    static constexpr int N = 84;
+    __device__ static constexpr int ox(int i) { return i < 42 ? ((i / 7) < 3 ? (i / 7) - 3 : (i / 7) - 2) : 0; }
+    __device__ static constexpr int oy(int i) {
+        return i < 42 ? 0 : (((i - 42) / 7) < 3 ? ((i - 42) / 7) - 3 : ((i - 42) / 7) - 2);
+    }
+    __device__ static constexpr int kk(int i) { return i < 42 ? i % 7 : (i - 42) % 7; }
+    __device__ static constexpr int slot(int i) { return i < 42 ? (ox(i) + 3) * 7 + i % 7 : 49 + ((i - 42) / 7) * 7 + (i - 42) % 7; }
+};
+
+// sum over the off-column slots whose neighbour colour satisfies pick(colour)
+template <int L, typename T, bool LOWER>
+__device__ __forceinline__ T off_column_sum(const Dev &D, const T *lu, const T *vals, int c, int ix, int iy, int j,
+                                            long long r) {
     const long long m = D.m;
-    const int col = col_of(D, c, q);
-    const int ix = col % D.nx, iy = col / D.nx;
-    const long long rbase = ((long long)c * (D.ncol >> 2) + q) * D.P;
-    T g[2];
-    int jl[2] = {lane - 1, lane + 31};
+    const int w0 = D.win[j + 1];
+    T acc = T(0);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        int j = jl[h];
-        g[h] = T(0);
-        if (j >= D.nz) continue;
-        long long r = rbase + j + 1;
-        T acc = T(in[(long long)(j + 1) * D.ncol + col]);
-        for (int s = 0; s < D.nslot; ++s) {
-            int nc, lev;
-            if (!off_slot(D, s, ix, iy, j, nc, lev)) continue;
-            if (colour_of(D, nc) >= c) continue;
-            acc -= lu[(long long)s * m + r] * out[(long long)(lev + 1) * D.ncol + nc];
-        }
-        g[h] = acc;
+    for (int i = 0; i < Off<L>::N; ++i) {
+        const int ox = Off<L>::ox(i), oy = Off<L>::oy(i);
+        const int nc = (c + ox + oy) & 3;
+        if (LOWER ? (nc >= c) : (nc <= c)) continue;
+        const int lev = Off<L>::kk(i) < 0 ? j : w0 + Off<L>::kk(i);
+        const int gx = wrapi(ix + ox, D.nx);
+        const int gy = (L == CROSS3D || L == BOX3D) ? wrapi(iy + oy, D.ny) : 0;
+        acc += lu[(long long)Off<L>::slot(i) * m + r] * vals[(long long)(lev + 1) * D.ncol + gy * D.nx + gx];
     }
-    // in-column recurrence
-    T lsig[2][W];
-    int w0[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        int j = jl[h];
-        w0[h] = (j < D.nz) ? D.win[j + 1] : 0;
-#pragma unroll
-        for (int k = 0; k < W; ++k)
-            lsig[h][k] = (j < D.nz) ? lu[(long long)sigma_slot(D.layout, k) * m + rbase + j + 1] : T(0);
-    }
-    for (int jj = -1; jj < D.nz; ++jj) {
-        int owner = (jj + 1) & 31, which = (jj + 1) >> 5;
-        T mine = which ? g[1] : g[0];
-        T yjj = __shfl_sync(0xffffffffu, mine, owner);
+    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ const T *linv_ptr(const Dev &D);
+template <> __device__ __forceinline__ const double *linv_ptr<double>(const Dev &D) { return D.linv64; }
+template <> __device__ __forceinline__ const float *linv_ptr<float>(const Dev &D) { return D.linv32; }
+template <typename T>
+__device__ __forceinline__ const T *uinv_ptr(const Dev &D);
+template <> __device__ __forceinline__ const double *uinv_ptr<double>(const Dev &D) { return D.uinv64; }
+template <> __device__ __forceinline__ const float *uinv_ptr<float>(const Dev &D) { return D.uinv32; }
+
+// y = B g for the column's P x P block inverse B (transposed storage bt[a2 * P + a]),
+// g held one level per lane (two slots per lane when P > 32).
+template <typename T>
+__device__ __forceinline__ void column_block_product(const T *bt, const T (&g)[2], T (&y)[2], int P, int lane) {
+    T a0[2] = {T(0), T(0)}, a1[2] = {T(0), T(0)};
+    const int a_h[2] = {lane, lane + 32};
+    int a2 = 0;
+    for (; a2 + 1 < P; a2 += 2) {
+        const T g0 = __shfl_sync(0xffffffffu, (a2 >> 5) ? g[1] : g[0], a2 & 31);
+        const T g1 = __shfl_sync(0xffffffffu, ((a2 + 1) >> 5) ? g[1] : g[0], (a2 + 1) & 31);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            int j = jl[h];
-            int kk = jj - w0[h];
-            if (j < D.nz && jj < j && kk >= 0) g[h] -= lsig[h][kk] * yjj;
+            if (a_h[h] < P) {
+                a0[h] += bt[a2 * P + a_h[h]] * g0;
+                a1[h] += bt[(a2 + 1) * P + a_h[h]] * g1;
+            }
         }
     }
+    if (a2 < P) {
+        const T g0 = __shfl_sync(0xffffffffu, (a2 >> 5) ? g[1] : g[0], a2 & 31);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (a_h[h] < P) a0[h] += bt[a2 * P + a_h[h]] * g0;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) y[h] = a0[h] + a1[h];
+}
+
+// forward (lower) sweep of one column of colour c; in -> out
+template <int L, typename T, typename TI>
+__device__ inline void ilu_fwd_column_t(const Dev &D, int c, int q, const TI *in, T *out, int lane) {
+    const T *lu = lu_ptr<T>(D);
+    const int col = col_of(D, c, q);
+    const int ix = col % D.nx, iy = col / D.nx;
+    const long long cr = (long long)c * (D.ncol >> 2) + q;
+    const long long rbase = cr * D.P;
+    T g[2], y[2];
+    const int jl[2] = {lane - 1, lane + 31};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        int j = jl[h];
-        if (j < D.nz) out[(long long)(j + 1) * D.ncol + col] = g[h];
+        const int j = jl[h];
+        g[h] = T(0);
+        if (j >= D.nz) continue;
+        g[h] = T(in[(long long)(j + 1) * D.ncol + col]) -
+               off_column_sum<L, T, true>(D, lu, out, c, ix, iy, j, rbase + j + 1);
     }
+    // in-column part: y = (unit lower block)^-1 g
+    column_block_product<T>(linv_ptr<T>(D) + cr * D.P * D.P, g, y, D.P, lane);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (jl[h] < D.nz) out[(long long)(jl[h] + 1) * D.ncol + col] = y[h];
 }
 
 // backward (upper) sweep of one column of colour c; in place on out
-template <typename T>
-__device__ inline void ilu_bwd_column(const Dev &D, int c, int q, T *out, int lane) {
+template <int L, typename T>
+__device__ inline void ilu_bwd_column_t(const Dev &D, int c, int q, T *out, int lane) {
     const T *lu = lu_ptr<T>(D);
-    const T *udi = udinv_ptr<T>(D);
-    const long long m = D.m;
     const int col = col_of(D, c, q);
     const int ix = col % D.nx, iy = col / D.nx;
-    const long long rbase = ((long long)c * (D.ncol >> 2) + q) * D.P;
-    T g[2], ud[2];
-    int jl[2] = {lane - 1, lane + 31};
+    const long long cr = (long long)c * (D.ncol >> 2) + q;
+    const long long rbase = cr * D.P;
+    T g[2], x[2];
+    const int jl[2] = {lane - 1, lane + 31};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        int j = jl[h];
+        const int j = jl[h];
         g[h] = T(0);
-        ud[h] = T(0);
         if (j >= D.nz) continue;
-        long long r = rbase + j + 1;
-        ud[h] = udi[r];
-        T acc = out[(long long)(j + 1) * D.ncol + col];
-        for (int s = 0; s < D.nslot; ++s) {
-            int nc, lev;
-            if (!off_slot(D, s, ix, iy, j, nc, lev)) continue;
-            if (colour_of(D, nc) <= c) continue;
-            acc -= lu[(long long)s * m + r] * out[(long long)(lev + 1) * D.ncol + nc];
-        }
-        g[h] = acc;
+        g[h] = out[(long long)(j + 1) * D.ncol + col] -
+               off_column_sum<L, T, false>(D, lu, out, c, ix, iy, j, rbase + j + 1);
     }
-    T usig[2][W];
-    int w0[2];
+    __syncwarp();
+    // in-column part: x = (upper block)^-1 g
+    column_block_product<T>(uinv_ptr<T>(D) + cr * D.P * D.P, g, x, D.P, lane);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        int j = jl[h];
-        w0[h] = (j < D.nz) ? D.win[j + 1] : 0;
-#pragma unroll
-        for (int k = 0; k < W; ++k)
-            usig[h][k] = (j < D.nz) ? lu[(long long)sigma_slot(D.layout, k) * m + rbase + j + 1] : T(0);
+    for (int h = 0; h < 2; ++h)
+        if (jl[h] < D.nz) out[(long long)(jl[h] + 1) * D.ncol + col] = x[h];
+}
+
+// runtime dispatch on the layout
+template <typename T, typename TI>
+__device__ inline void ilu_fwd_column(const Dev &D, int c, int q, const TI *in, T *out, int lane) {
+    switch (D.layout) {
+    case CROSS2D: ilu_fwd_column_t<CROSS2D, T, TI>(D, c, q, in, out, lane); break;
+    case BOX2D: ilu_fwd_column_t<BOX2D, T, TI>(D, c, q, in, out, lane); break;
+    case CROSS3D: ilu_fwd_column_t<CROSS3D, T, TI>(D, c, q, in, out, lane); break;
+    default: ilu_fwd_column_t<BOX3D, T, TI>(D, c, q, in, out, lane); break;
     }
-    T xv[2] = {T(0), T(0)};
-    for (int jj = D.nz - 1; jj >= -1; --jj) {
-        int owner = (jj + 1) & 31, which = (jj + 1) >> 5;
-        T cand = which ? g[1] * ud[1] : g[0] * ud[0];
-        T xjj = __shfl_sync(0xffffffffu, cand, owner);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int j = jl[h];
-            if (j >= D.nz) continue;
-            if (j == jj) xv[h] = xjj;
-            int kk = jj - w0[h];
-            if (jj > j && kk < W) g[h] -= usig[h][kk] * xjj;
-        }
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        int j = jl[h];
-        if (j < D.nz) out[(long long)(j + 1) * D.ncol + col] = xv[h];
+}
+template <typename T>
+__device__ inline void ilu_bwd_column(const Dev &D, int c, int q, T *out, int lane) {
+    switch (D.layout) {
+    case CROSS2D: ilu_bwd_column_t<CROSS2D, T>(D, c, q, out, lane); break;
+    case BOX2D: ilu_bwd_column_t<BOX2D, T>(D, c, q, out, lane); break;
+    case CROSS3D: ilu_bwd_column_t<CROSS3D, T>(D, c, q, out, lane); break;
+    default: ilu_bwd_column_t<BOX3D, T>(D, c, q, out, lane); break;
     }
 }
 
@@ -409,9 +458,15 @@ __device__ __forceinline__ void warp_reduce_scatter(double (&v)[N], int lane) {
 }
 
 // Block-reduce n <= 32 values (v[i], i >= n ignored) into part[v * nb + blockIdx.x].
-__device__ inline void block_partials32(double (&v)[32], int n, double *red, double *part, int nb) {
+// Warps that hold no data (active == false) contribute zeros without FP64 work.
+__device__ inline void block_partials32(double (&v)[32], int n, double *red, double *part, int nb,
+                                        bool active = true) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (n <= 4) {
+    if (!active) {
+        red[warp * 32 + lane] = 0.0;
+    } else if (n <= 4) {
+        red[warp * 32 + lane] = 0.0;
+        __syncwarp();
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (i >= n) break;
@@ -434,15 +489,33 @@ __device__ inline void block_partials32(double (&v)[32], int n, double *red, dou
     __syncthreads();
 }
 
-// After a grid barrier: every block sums value i over the blocks into out[i].
-__device__ inline void gather_partials(const double *part, int n, int nb, double *out) {
+// After a grid barrier: every block sums value i over the blocks into out[i]
+// (n <= 32).  Lane i of warp w adds the partials of blocks w, w + 8, ...; all
+// loads are issued before the adds, then the warps are combined.
+constexpr int GATHER_PER_WARP = 20;   // supports up to 160 blocks
+__device__ inline void gather_partials(const double *part, int n, int nb, double *out, double *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < n; i += NWARPS) {
-        double s = 0.0;
-        for (int b = lane; b < nb; b += 32) s += part[i * nb + b];
+    double t[GATHER_PER_WARP];
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) out[i] = s;
+    for (int u = 0; u < GATHER_PER_WARP; ++u) {
+        const int b = warp + NWARPS * u;
+        t[u] = (b < nb && lane < n) ? part[lane * nb + b] : 0.0;
+    }
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+#pragma unroll
+    for (int u = 0; u < GATHER_PER_WARP; u += 4) {
+        a += t[u];
+        b += t[u + 1];
+        c += t[u + 2];
+        d += t[u + 3];
+    }
+    red[warp * 32 + lane] = (a + b) + (c + d);
+    __syncthreads();
+    if (warp == 0) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NWARPS; ++w) s += red[w * 32 + lane];
+        if (lane < n) out[lane] = s;
     }
     __syncthreads();
 }

@@ -45,6 +45,10 @@ struct Dev {
     const float *lu32;                     // same, FP32 copy (mixed precision)
     const double *udinv64;                 // 1 / u_jj per rank
     const float *udinv32;
+    // Per-column inverses of the in-column blocks of L and U (P x P each),
+    // transposed: blk[(colrank * P + jp) * P + j] = inv[j][jp].
+    const double *linv64, *uinv64;
+    const float *linv32, *uinv32;
 };
 
 // Algorithmic cost per grid point of the building blocks (FP64 words).
@@ -69,6 +73,8 @@ struct Problem {
     double *d_geom = nullptr;      // per-column coefficients (20 x ncol)
     double *d_lu64 = nullptr, *d_udinv64 = nullptr;
     float *d_lu32 = nullptr, *d_udinv32 = nullptr;
+    double *d_linv64 = nullptr, *d_uinv64 = nullptr;
+    float *d_linv32 = nullptr, *d_uinv32 = nullptr;
     double *d_V = nullptr;         // (restart + 1) x m Krylov basis
     float *d_V32 = nullptr;
     double *d_work = nullptr;      // 6 x m work vectors
@@ -111,6 +117,7 @@ struct DevStats {
     int guess_rank, guess_mode, cholesky_shift, pad;
     long long total_iterations;
     double model_flops, model_bytes;
+    double phase_ns[16];   // cumulative device time per solve phase (block 0's view)
 };
 
 
