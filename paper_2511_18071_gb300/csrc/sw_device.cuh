@@ -460,7 +460,8 @@ __device__ __forceinline__ void warp_reduce_scatter(double (&v)[N], int lane) {
 // Block-reduce n <= 32 values (v[i], i >= n ignored) into part[v * nb + blockIdx.x].
 // Warps that hold no data (active == false) contribute zeros without FP64 work.
 __device__ inline void block_partials32(double (&v)[32], int n, double *red, double *part, int nb,
-                                        bool active = true) {
+                                        bool active = true, int off = -1) {
+    if (off < 0) off = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (!active) {
         red[warp * 32 + lane] = 0.0;
@@ -484,7 +485,7 @@ __device__ inline void block_partials32(double (&v)[32], int n, double *red, dou
         double s = 0.0;
         if (lane < n)
             for (int w = 0; w < NWARPS; ++w) s += red[w * 32 + lane];
-        if (lane < n) part[lane * nb + blockIdx.x] = s;
+        if (lane < n) part[lane * nb + off] = s;
     }
     __syncthreads();
 }

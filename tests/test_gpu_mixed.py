@@ -1,0 +1,92 @@
+"""Precision form: FP32 operator, preconditioner and Krylov vectors inside each
+restart cycle, FP64 residual, Gram-Schmidt coefficients, Givens and subspace
+least squares.  The FP64-refined solution must match the FP64 oracle: run to
+1e-12, ||x - x_ref|| <= 1e-10 ||x_ref||; run to 1e-8, both meet the tolerance
+and the solutions agree to the conditioning of the system (<= 1e-6 here)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def sw():
+    from paper_2511_18071_gb300 import build
+    build.build()
+    import paper_2511_18071_gb300 as sw
+    return sw
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
+
+
+def _cases():
+    L = 2 * math.pi
+    x64 = np.arange(64) * (L / 64)
+    X, Y = np.meshgrid(np.arange(16) * (L / 16), np.arange(8) * (L / 8), indexing="xy")
+    return [("flat2d", 64, 1, 9, L, 0.0, np.ones(64)),
+            ("bar2d", 64, 1, 9, L, 0.0, 1.0 - 0.4 * np.exp(-3 * (x64 - 3.0) ** 2)),
+            ("bumpy3d", 16, 8, 9, L, L, (1.0 + 0.2 * np.exp(-((X - 3) ** 2 + (Y - 2) ** 2))).ravel())]
+
+
+def _surfaces(nx, ny, seed):
+    rng = np.random.default_rng(seed)
+    L = 2 * math.pi
+    X, Y = np.meshgrid(np.arange(nx) * (L / nx), np.arange(ny) * (L / ny), indexing="xy")
+    e1 = (0.03 * np.cos(X + rng.uniform(0, 6)) + 0.01 * np.sin(2 * X + Y)).ravel()
+    e2 = e1 + (0.002 * np.cos(X + Y + rng.uniform(0, 6))).ravel()
+    return e1, e2
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
+def test_mixed_refined_solution_matches_fp64_oracle(sw, case):
+    name, nx, ny, nz, lx, ly, h = case
+    kw = dict(restart=20, max_restarts=400, tol=1e-12, guess="cold")
+    gpu = sw.Problem(nx, ny, nz, lx, ly, h, precision="mixed", **kw)
+    ora = O.OracleProblem(nx, ny, nz, lx, ly, h, **kw)
+    e1, e2 = _surfaces(nx, ny, 4)
+    b = np.random.default_rng(5).standard_normal(ora.m)
+    b[ora.index(0, 0, nz - 1):] = 0.0
+    xo, so, co = ora.solve(e1, e2, b)
+    x = torch.zeros(gpu.m, dtype=torch.float64, device=DEV)
+    gpu.solve(_t(e1), _t(e2), _t(b), x)
+    sg = gpu.stats()
+    assert co == 0 and sg["status"] == 0, (so, sg)
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err <= 1e-10, (name, err, so["iterations"], sg["iterations"])
+
+
+def test_mixed_trajectory_meets_tolerance(sw):
+    wl = W.airy_2d()
+    kw = dict(restart=20, max_restarts=100, tol=1e-8, guess="ewma", k=8, decay=0.9, n_init_solves=10)
+    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], precision="mixed", **kw)
+    ora = O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
+    st = W.state_arrays(wl)
+    phys = (wl["g"], wl["rho"], wl["dt"])
+    al, be, _ = O.lserk45()
+    x = torch.zeros(gpu.m, dtype=torch.float64, device=DEV)
+    its_g, its_o = 0, 0
+    for _ in range(6):
+        for i in range(1, 6):
+            feta = ora.f_eta(st["u"], st["v"], st["w"], st["eta"])
+            eta_new = st["eta"] + be[i - 1] * (al[i - 1] * st["Keta"] + wl["dt"] * feta)
+            b = ora.rhs(phys, i, st["u"], st["v"], st["w"], st["Ku"], st["Kv"], st["Kw"], st["eta"], eta_new, feta)
+            ep = st["eta"].copy()
+            p, so, code = ora.stage(phys, i, st)
+            gpu.solve(_t(ep), _t(eta_new), _t(b), x)
+            sg = gpu.stats()
+            assert sg["status"] == 0 and sg["res_final"] <= 1.0000001e-8, sg
+            err = np.linalg.norm(x.cpu().numpy() - p) / np.linalg.norm(p)
+            assert err < 1e-6, err
+            its_g += sg["iterations"]
+            its_o += so["iterations"]
+    assert its_g <= 1.5 * its_o + 10, (its_g, its_o)
