@@ -166,6 +166,25 @@ int sw_advance_stage(sw_problem *p, void *stream);
 /* The system A(eta_prev, eta_cur) p = b of the last stage (copies; any pointer may be NULL). */
 int sw_get_last_system(sw_problem *p, double *d_eta_prev, double *d_eta_cur, double *d_b, void *stream);
 
+/* ---- batch form: many independent problems in one launch per step ---- */
+
+typedef struct sw_batch sw_batch;
+
+/* Group existing problems (all with the same precision) so that their solves
+ * and stages run together: each Poisson solve on one thread block, problems
+ * handed out largest first; each driver step one launch over (problem, node).
+ * The batch keeps pointers to the problems, which must outlive it.  The
+ * many-query setting of Sec. 1 (many wave simulations at once) is the use. */
+int sw_create_batch(sw_problem *const *problems, int n, sw_batch **out);
+int sw_destroy_batch(sw_batch *b);
+/* Solve every member's system A_i x_i = b_i (Algorithm 2 per member, as
+ * sw_solve_poisson).  Host arrays of n device pointers, in the order the
+ * problems were given to sw_create_batch.  Per-member results via sw_get_stats. */
+int sw_batch_solve(sw_batch *b, const double *const *d_eta_prev, const double *const *d_eta_cur,
+                   const double *const *d_b, double *const *d_x, void *stream);
+/* One Runge-Kutta stage of every member (each needs its state and physics set). */
+int sw_batch_advance_stage(sw_batch *b, void *stream);
+
 /* Allocation-free operator apply: y = A(eta_prev, eta_cur) x as in
  * sw_apply_operator, but without a problem handle and without allocating
  * device memory.  The paper has no counterpart; this exists for callers that

@@ -14,7 +14,8 @@ from . import build as _build
 __all__ = ["Grid", "Params", "Stats", "Physics", "Problem", "create_problem", "destroy_problem", "problem_size",
            "solve_poisson", "solve_poisson_host", "get_stats", "apply_operator", "apply_preconditioner",
            "subspace_guess", "apply_operator_noalloc", "get_sketch", "set_sketch", "draw_omega", "set_physics", "set_state", "get_state",
-           "advance_stage", "get_last_system", "get_phase_times", "enable_timing", "get_solve_time", "library_path", "SawaveError", "GUESS",
+           "advance_stage", "create_batch", "destroy_batch", "batch_solve", "batch_advance_stage", "Batch",
+           "get_last_system", "get_phase_times", "enable_timing", "get_solve_time", "library_path", "SawaveError", "GUESS",
            "PRECISION"]
 
 SW_OK = 0
@@ -90,13 +91,18 @@ def lib():
         L.sw_get_last_system.argtypes = [vp, vp, vp, vp, vp]
         L.sw_apply_operator_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp, vp, vp, vp]
         L.sw_get_phase_times.argtypes = [vp, vp, ip]
+        L.sw_create_batch.argtypes = [vp, ip, C.POINTER(vp)]
+        L.sw_destroy_batch.argtypes = [vp]
+        L.sw_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sw_batch_advance_stage.argtypes = [vp, vp]
         L.sw_get_solve_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
         L.sw_last_error.restype = C.c_char_p
         for name in ["sw_create_problem", "sw_destroy_problem", "sw_problem_size", "sw_solve_poisson",
                      "sw_solve_poisson_host", "sw_get_stats", "sw_apply_operator", "sw_apply_preconditioner",
                      "sw_subspace_guess", "sw_get_sketch", "sw_set_sketch", "sw_draw_omega", "sw_set_physics",
                      "sw_set_state", "sw_get_state", "sw_advance_stage", "sw_enable_timing", "sw_get_solve_time",
-                     "sw_get_last_system", "sw_apply_operator_noalloc", "sw_get_phase_times"]:
+                     "sw_get_last_system", "sw_apply_operator_noalloc", "sw_get_phase_times", "sw_create_batch",
+                     "sw_destroy_batch", "sw_batch_solve", "sw_batch_advance_stage"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -250,6 +256,58 @@ def get_solve_time(p):
     ms, n = C.c_double(), C.c_longlong()
     _check(lib().sw_get_solve_time(p, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def _ptr_array(tensors):
+    arr = (C.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = _dptr(t).value
+    return arr
+
+
+def create_batch(problems):
+    arr = (C.c_void_p * len(problems))(*[p.handle.value if hasattr(p, "handle") else p.value for p in problems])
+    out = C.c_void_p()
+    _check(lib().sw_create_batch(arr, len(problems), C.byref(out)))
+    return out
+
+
+def destroy_batch(b):
+    return _check(lib().sw_destroy_batch(b))
+
+
+def batch_solve(b, eta_prev, eta_cur, rhs, x, stream=None):
+    return _check(lib().sw_batch_solve(b, _ptr_array(eta_prev), _ptr_array(eta_cur), _ptr_array(rhs), _ptr_array(x),
+                                       _stream(stream)))
+
+
+def batch_advance_stage(b, stream=None):
+    return _check(lib().sw_batch_advance_stage(b, _stream(stream)))
+
+
+class Batch:
+    """Owning handle around sw_batch; keeps its problems alive."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        self.handle = create_batch(self.problems)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, eta_prev, eta_cur, rhs, x, stream=None):
+        return batch_solve(self.handle, eta_prev, eta_cur, rhs, x, stream)
+
+    def advance_stage(self, stream=None):
+        return batch_advance_stage(self.handle, stream)
 
 
 class Problem:

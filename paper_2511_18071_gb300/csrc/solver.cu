@@ -26,32 +26,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) 
     solve_body<GridTeam, TI>(tm, D, A, S, smem_raw + SMEM_FIXED, ph);
 }
 
-// Batches: one block per instance, instances handed out by an atomic counter
-// (the host orders them largest first).
-struct BatchItem {
-    Dev D;
-    SolveArgs A;
-};
-
-template <typename TI>
-__global__ void __launch_bounds__(NTHREADS, 1) batch_solve_kernel(const BatchItem *items, int n, int *counter) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemFixed &S = *reinterpret_cast<SmemFixed *>(smem_raw);
-    __shared__ int idx;
-    for (;;) {
-        if (threadIdx.x == 0) idx = atomicAdd(counter, 1);
-        __syncthreads();
-        const int i = idx;
-        __syncthreads();
-        if (i >= n) break;
-        const Dev D = items[i].D;
-        const SolveArgs A = items[i].A;
-        BlockTeam tm;
-        solve_body<BlockTeam, TI>(tm, D, A, S, smem_raw + SMEM_FIXED, nullptr);
-        __syncthreads();
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Standalone kernels for the per-step entry points.
 // ---------------------------------------------------------------------------

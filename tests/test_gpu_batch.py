@@ -1,0 +1,121 @@
+"""Batch form: many independent problems of uneven size solved in one launch,
+one thread block per problem, against the oracle problem by problem.
+Solves run to 1e-12 agree with the oracle to 1e-10 (FP64 and the FP64-refined
+precision form); the batched stage driver tracks the oracle's stages to 1e-9;
+EWMA iteration counts at 1e-8 match the single-problem path to +-1."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def sw():
+    from paper_2511_18071_gb300 import build
+    build.build()
+    import paper_2511_18071_gb300 as sw
+    return sw
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
+
+
+def _members():
+    L = 2 * math.pi
+    out = []
+    for i, (nx, nz, bar) in enumerate([(32, 7, False), (64, 9, True), (128, 17, False), (48, 9, True), (96, 33, False)]):
+        x = np.arange(nx) * (L / nx)
+        h = 1.0 - (0.35 * np.exp(-3 * (x - 2.0 - 0.3 * i) ** 2) if bar else 0.0 * x)
+        out.append((nx, nz, L, h))
+    return out
+
+
+def _surfaces(nx, seed):
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx) * (2 * math.pi / nx)
+    e1 = 0.03 * np.cos(x + rng.uniform(0, 6)) + 0.01 * np.sin(2 * x)
+    return e1, e1 + 0.002 * np.cos(3 * x + rng.uniform(0, 6))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_solve_matches_oracle(sw, precision):
+    kw = dict(restart=20, max_restarts=400, tol=1e-12, guess="cold")
+    mem = _members()
+    probs = [sw.Problem(nx, 1, nz, L, 0.0, h, precision=precision, **kw) for nx, nz, L, h in mem]
+    batch = sw.Batch(probs)
+    eps, ecs, bs, xs, refs = [], [], [], [], []
+    for i, (nx, nz, L, h) in enumerate(mem):
+        ora = O.OracleProblem(nx, 1, nz, L, 0.0, h, **kw)
+        e1, e2 = _surfaces(nx, i)
+        b = np.random.default_rng(10 + i).standard_normal(ora.m)
+        b[ora.index(0, 0, nz - 1):] = 0.0
+        xo, so, co = ora.solve(e1, e2, b)
+        assert co == 0
+        refs.append(xo)
+        eps.append(_t(e1)); ecs.append(_t(e2)); bs.append(_t(b))
+        xs.append(torch.zeros(ora.m, dtype=torch.float64, device=DEV))
+    batch.solve(eps, ecs, bs, xs)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        st = p.stats()
+        assert st["status"] == 0, (i, st)
+        err = np.linalg.norm(xs[i].cpu().numpy() - refs[i]) / np.linalg.norm(refs[i])
+        assert err <= 1e-10, (i, err)
+
+
+def test_batch_stage_driver_matches_oracle(sw):
+    kw = dict(restart=20, max_restarts=200, tol=1e-12, guess="previous")
+    wls = [W.airy_2d(nx=64, nz=9), W.airy_2d(nx=32, nz=7, kh=0.7), W.periodic_bar_2d(nx=64, nz=9)]
+    probs, oras, states = [], [], []
+    for wl in wls:
+        p = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
+        sw.set_physics(p.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+        sw.set_state(p.handle, _t(wl["u"]), None, _t(wl["w"]), _t(wl["eta"]))
+        probs.append(p)
+        oras.append(O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw))
+        states.append(W.state_arrays(wl))
+    batch = sw.Batch(probs)
+    for step in range(2):
+        for i in range(1, 6):
+            batch.advance_stage()
+            for wl, p, ora, st in zip(wls, probs, oras, states):
+                pr, so, code = ora.stage((wl["g"], wl["rho"], wl["dt"]), i, st)
+                eta = torch.empty(p.ncol, dtype=torch.float64, device=DEV)
+                u = torch.empty(p.m, dtype=torch.float64, device=DEV)
+                pp = torch.empty_like(u)
+                sw.get_state(p.handle, u=u, eta=eta, pres=pp)
+                torch.cuda.synchronize()
+                for name, g_, o_ in [("eta", eta, st["eta"]), ("u", u, st["u"]), ("p", pp, pr)]:
+                    err = np.abs(g_.cpu().numpy() - o_).max() / max(np.abs(o_).max(), 1e-300)
+                    assert err < 1e-9, (wl["name"], step, i, name, err)
+
+
+def test_batch_ewma_iterations_match_single(sw):
+    kw = dict(restart=20, max_restarts=200, tol=1e-8, guess="ewma", k=6, decay=0.9, n_init_solves=5)
+    wls = [W.airy_2d(nx=64, nz=9), W.periodic_bar_2d(nx=64, nz=9)]
+    def make():
+        ps = []
+        for wl in wls:
+            p = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
+            sw.set_physics(p.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+            sw.set_state(p.handle, _t(wl["u"]), None, _t(wl["w"]), _t(wl["eta"]))
+            ps.append(p)
+        return ps
+    single, batched = make(), make()
+    batch = sw.Batch(batched)
+    for _ in range(4 * 5):
+        batch.advance_stage()
+        for p in single:
+            sw.advance_stage(p.handle)
+        for a, b in zip(single, batched):
+            sa, sb = a.stats(), b.stats()
+            assert sa["status"] == 0 and sb["status"] == 0
+            assert abs(sa["iterations"] - sb["iterations"]) <= 1, (sa, sb)
