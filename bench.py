@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--members", type=int, default=512, help="batch512: number of instances")
+    ap.add_argument("--workload", default="stokes512", choices=["stokes512", "bumpy3d", "batch512"],
+                    help="stokes512: the headline 512 x 17 steep wave (FP64); bumpy3d: 256 x 256 x 17 "
+                         "precision form vs FP64; batch512: 512 uneven instances, batched vs one by one")
     return ap.parse_args()
 
 
@@ -282,6 +286,12 @@ def gpu_arm(args, rank, world, local_rank):
                        "ms_per_solve": ms / n, "steps": args.plain_steps,
                        "phase_us_per_iteration": {k: round((qp1[k] - qp0[k]) / max(nit, 1), 2) for k in qp1}}
         Q.close()
+    # ---- the precision form on the same trajectory ----
+    Mx = _make(sw, torch, dev, wl, "ewma", "mixed", args)
+    run_steps(sw, torch, Mx, args.warmup)
+    torch.cuda.synchronize()
+    mixed_res = _timed_steps(sw, torch, Mx, args.steps, flush)
+    Mx.close()
     # ---- end to end through the host-buffer C-ABI call ----
     e2e = None
     if not args.no_e2e:
@@ -346,6 +356,7 @@ def gpu_arm(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "iters_per_solve": its, "us_per_solve": 1e3 * total_ms / nsolves,
             "plain": base["cold"], "previous": base["previous"],
+            "mixed": {k: mixed_res[k] for k in ("value", "iters_per_solve", "ms_per_step")},
             "speedup_vs_plain": value / base["cold"]["value"] / world,
             "config": {"workload": WORKLOAD, "nx": 512, "nz": 17, "unknowns": wl["m"], "guess": "ewma", "k": args.k,
                        "decay": args.decay, "tol": 1e-8, "restart": 20, "n_init_steps": 6, "dt": wl["dt"],
@@ -357,8 +368,166 @@ def gpu_arm(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def _t(torch, dev, a):
+    import numpy as np
+    return torch.tensor(np.ascontiguousarray(a), device=dev)
+
+
+def _make(sw, torch, dev, wl, guess, precision, args):
+    P = sw.Problem(wl["nx"], wl["ny"], wl["nz"], wl["lx"], wl["ly"], wl["h"], precision=precision,
+                   **solver_kw(args, guess))
+    sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+    v = None if wl["v"] is None else _t(torch, dev, wl["v"])
+    sw.set_state(P.handle, _t(torch, dev, wl["u"]), v, _t(torch, dev, wl["w"]), _t(torch, dev, wl["eta"]))
+    return P
+
+
+def _timed_steps(sw, torch, P, steps, flush):
+    s0 = sw.get_stats(P.handle)
+    ph0 = sw.get_phase_times(P.handle)
+    sw.enable_timing(P.handle, True)
+    ev = []
+    run_steps(sw, torch, P, steps, flush=flush, events=ev)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    kms, kn = sw.get_solve_time(P.handle)
+    sw.enable_timing(P.handle, False)
+    s1 = sw.get_stats(P.handle)
+    ph1 = sw.get_phase_times(P.handle)
+    n = 5 * steps
+    return dict(value=n / (ms / 1e3), ms_per_step=ms / steps, iters_per_solve=(s1["total_iterations"] - s0["total_iterations"]) / n,
+                kernel_ms=kms, kernel_launches=kn, flops=s1["model_flops"] - s0["model_flops"],
+                bytes=s1["model_bytes"] - s0["model_bytes"], launches=s1["launches"] - s0["launches"],
+                phase_us_per_solve={k: round((ph1[k] - ph0[k]) / n, 2) for k in ph1})
+
+
+def bumpy3d_arm(args):
+    """256 x 256 x 17 periodic field over bumps: precision form vs plain FP64 (EWMA both)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    import workloads as W
+    ge.build()
+    import paper_2511_18071_gb300 as sw
+    dev = torch.device("cuda", 0)
+    wl = W.bumpy_3d()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    last = {}
+    for prec in ("mixed", "fp64"):
+        t0 = time.perf_counter()
+        P = _make(sw, torch, dev, wl, "ewma", prec, args)
+        create_s = time.perf_counter() - t0
+        run_steps(sw, torch, P, args.warmup)
+        torch.cuda.synchronize()
+        with ClockSampler(0) as clk:
+            r = _timed_steps(sw, torch, P, args.steps, flush)
+        r["create_s"] = create_s
+        r["clocks"] = clk.summary()
+        ep = torch.empty(P.ncol, dtype=torch.float64, device=dev)
+        ec = torch.empty_like(ep)
+        b = torch.empty(P.m, dtype=torch.float64, device=dev)
+        sw.get_last_system(P.handle, ep, ec, b)
+        last[prec] = (ep, ec, b)
+        res[prec] = r
+        P.close()
+    # error of a mixed solve against an FP64 solve of the same system, both to 1e-8
+    ep, ec, b = last["mixed"]
+    xs = {}
+    for prec in ("mixed", "fp64"):
+        Q = sw.Problem(wl["nx"], wl["ny"], wl["nz"], wl["lx"], wl["ly"], wl["h"], precision=prec,
+                       **dict(solver_kw(args, "cold"), tol=1e-10))
+        x = torch.zeros(Q.m, dtype=torch.float64, device=dev)
+        Q.solve(ep, ec, b, x)
+        torch.cuda.synchronize()
+        xs[prec] = x.cpu().numpy()
+        Q.close()
+    err = float(np.linalg.norm(xs["mixed"] - xs["fp64"]) / np.linalg.norm(xs["fp64"]))
+    peaks = load_peaks()
+    mx = res["mixed"]
+    ach = mx["bytes"] / (mx["kernel_ms"] / 1e3) / 1e9
+    line = {"metric": METRIC, "value": mx["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "iters_per_solve": mx["iters_per_solve"],
+            "fp64": res["fp64"], "mixed": mx, "speedup_vs_fp64": mx["value"] / res["fp64"]["value"],
+            "mixed_vs_fp64_rel_error_tol1e-10": err,
+            "roofline": {"kernel": "solve_kernel<float>", "bound": "hbm", "achieved": ach,
+                         "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None, "traffic": None},
+            "config": {"workload": "bumpy3d_256x256x17", "unknowns": wl["m"], "guess": "ewma", "k": args.k,
+                       "decay": args.decay, "tol": 1e-8, "restart": 20,
+                       "l2": "inputs larger than L2 and flushed between timed steps"}}
+    print(json.dumps(line), flush=True)
+
+
+def batch512_arm(args):
+    """512 uneven 2-D instances: one batched launch per step vs the same instances one by one."""
+    import concurrent.futures as cf
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    import workloads as W
+    ge.build()
+    import paper_2511_18071_gb300 as sw
+    dev = torch.device("cuda", 0)
+    members = W.batch_members(n=args.members)
+    prec = "mixed"
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        probs = list(ex.map(lambda wl: sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], precision=prec,
+                                                   **solver_kw(args, "ewma")), members))
+    create_s = time.perf_counter() - t0
+    for P, wl in zip(probs, members):
+        sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+        sw.set_state(P.handle, _t(torch, dev, wl["u"]), None, _t(torch, dev, wl["w"]), _t(torch, dev, wl["eta"]))
+    B = sw.Batch(probs)
+    for _ in range(args.warmup * 5):
+        B.advance_stage()
+    torch.cuda.synchronize()
+    it0 = sum(sw.get_stats(P.handle)["total_iterations"] for P in probs)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        a.record()
+        for _ in range(args.steps * 5):
+            B.advance_stage()
+        b.record()
+        torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    it1 = sum(sw.get_stats(P.handle)["total_iterations"] for P in probs)
+    nsolve = len(probs) * 5 * args.steps
+    batched = nsolve / (ms / 1e3)
+    # the same instances advanced one by one (one step) with the single-problem API
+    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a2.record()
+    for P in probs:
+        for _ in range(5):
+            sw.advance_stage(P.handle)
+    b2.record()
+    torch.cuda.synchronize()
+    ms1 = a2.elapsed_time(b2)
+    single = len(probs) * 5 / (ms1 / 1e3)
+    line = {"metric": METRIC, "value": batched, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "iters_per_solve": (it1 - it0) / nsolve,
+            "one_by_one": {"value": single, "steps": 1}, "speedup_vs_one_by_one": batched / single,
+            "create_s": create_s, "clocks": clk.summary(), "gpu_launches_per_step": 5 * 7,
+            "config": {"workload": "batch512_uneven_2d", "instances": len(probs),
+                       "unknowns_total": int(sum(wl["m"] for wl in members)), "guess": "ewma", "k": args.k,
+                       "decay": args.decay, "tol": 1e-8, "restart": 20, "precision": prec}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "bumpy3d":
+        bumpy3d_arm(args)
+        return
+    if args.workload == "batch512":
+        batch512_arm(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

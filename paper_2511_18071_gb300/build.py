@@ -15,7 +15,7 @@ LIB = os.path.join(OUT, "libsawave.so")
 SOURCES = ["setup.cu", "solver.cu", "driver.cu", "batch.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-         "--expt-relaxed-constexpr"]
+         "-Xcompiler", "-pthread", "--expt-relaxed-constexpr"]
 
 
 def nvcc():
@@ -52,7 +52,7 @@ def build(force=False, verbose=False):
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(comp, SOURCES))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <algorithm>
 #include <new>
+#include <thread>
 
 #include "sw_internal.cuh"
 
@@ -222,14 +223,13 @@ struct Host {
 // ILU(0), row by row in rank order (IKJ form): for each row i and each entry
 // k < i of its pattern in increasing order, l_ik = a_ik / u_kk, then
 // a_ij -= l_ik u_kj for every j > k present in both row k and row i.
-static int factorise(const Host &H, std::vector<double> &lu, std::vector<double> &udinv) {
+// Rows of one column are consecutive ranks and only reference lower colours
+// or the same column, so the columns of one colour are factorised in parallel.
+static void factorise_column(const Host &H, int c, int q, std::vector<double> &lu, std::vector<double> &udinv,
+                             std::vector<double> &v, std::vector<std::pair<long long, int>> &lower, int &status) {
     const int ns = H.nslot;
-    const long long m = H.m;
-    lu.assign((size_t)m * ns, 0.0);       // row-major during the factorisation
-    udinv.assign((size_t)m, 0.0);
-    std::vector<double> v(ns);
-    std::vector<std::pair<long long, int>> lower;
-    for (long long i = 0; i < m; ++i) {
+    for (int a = 0; a < H.P; ++a) {
+        const long long i = ((long long)c * (H.ncol / 4) + q) * H.P + a;
         int ix, iy, j;
         H.node_of_rank(i, ix, iy, j);
         H.a0_row(ix, iy, j, v.data());
@@ -243,9 +243,9 @@ static int factorise(const Host &H, std::vector<double> &lu, std::vector<double>
         }
         std::sort(lower.begin(), lower.end());
         for (auto &ks : lower) {
-            long long k = ks.first;
-            int s = ks.second;
-            double l = v[s] * udinv[k];
+            const long long k = ks.first;
+            const int s = ks.second;
+            const double l = v[s] * udinv[k];
             v[s] = l;
             int kx, ky, kj;
             H.node_of_rank(k, kx, ky, kj);
@@ -260,10 +260,38 @@ static int factorise(const Host &H, std::vector<double> &lu, std::vector<double>
                 v[s3] -= l * rowk[s2];
             }
         }
-        double ud = v[sigma_slot(H.layout, j - H.win[j + 1])];
-        if (ud == 0.0 || !std::isfinite(ud)) return SW_ERR_SINGULAR_PRECOND;
+        const double ud = v[sigma_slot(H.layout, j - H.win[j + 1])];
+        if (ud == 0.0 || !std::isfinite(ud)) { status = SW_ERR_SINGULAR_PRECOND; return; }
         udinv[i] = 1.0 / ud;
         std::copy(v.begin(), v.end(), lu.begin() + (size_t)i * ns);
+    }
+}
+
+static int factorise(const Host &H, std::vector<double> &lu, std::vector<double> &udinv) {
+    const int ns = H.nslot;
+    const long long m = H.m;
+    lu.assign((size_t)m * ns, 0.0);   // row-major during the factorisation
+    udinv.assign((size_t)m, 0.0);
+    const int per = H.ncol / 4;
+    unsigned hw = std::thread::hardware_concurrency();
+    int nt = (int)std::max(1u, std::min(hw ? hw : 1u, 32u));
+    if (m < 20000) nt = 1;
+    std::vector<int> status(nt, SW_OK);
+    for (int c = 0; c < 4; ++c) {
+        auto work = [&](int t) {
+            std::vector<double> v(ns);
+            std::vector<std::pair<long long, int>> lower;
+            for (int q = t; q < per && status[t] == SW_OK; q += nt) factorise_column(H, c, q, lu, udinv, v, lower, status[t]);
+        };
+        if (nt == 1) {
+            work(0);
+        } else {
+            std::vector<std::thread> th;
+            for (int t = 0; t < nt; ++t) th.emplace_back(work, t);
+            for (auto &x : th) x.join();
+        }
+        for (int t = 0; t < nt; ++t)
+            if (status[t] != SW_OK) return status[t];
     }
     return SW_OK;
 }
@@ -426,6 +454,8 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     ALLOC(P->d_win, H.P * sizeof(int));
     ALLOC(P->d_hcols, 5 * (size_t)H.ncol * sizeof(double));
     ALLOC(P->d_geom, 20 * (size_t)H.ncol * sizeof(double));
+    ALLOC(P->d_geom32, 20 * (size_t)H.ncol * sizeof(float));
+    ALLOC(P->d_weights32, wts.size() * sizeof(float));
     ALLOC(P->d_lu64, (size_t)m * ns * sizeof(double));
     ALLOC(P->d_udinv64, (size_t)m * sizeof(double));
     ALLOC(P->d_lu32, (size_t)m * ns * sizeof(float));
@@ -446,6 +476,11 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     ALLOC(P->d_host_io, (3 * (size_t)m + 2 * (size_t)H.ncol) * sizeof(double));
     e = cudaMemcpy(P->d_weights, wts.data(), wts.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->d_win, H.win.data(), H.P * sizeof(int), cudaMemcpyHostToDevice);
+    {
+        std::vector<float> w32(wts.begin(), wts.end());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->d_weights32, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     std::vector<double> hc(5 * (size_t)H.ncol);
     std::copy(H.h.begin(), H.h.end(), hc.begin());
     std::copy(H.hx.begin(), H.hx.end(), hc.begin() + H.ncol);
@@ -453,16 +488,21 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     std::copy(H.hxx.begin(), H.hxx.end(), hc.begin() + 3 * H.ncol);
     std::copy(H.hyy.begin(), H.hyy.end(), hc.begin() + 4 * H.ncol);
     if (e == cudaSuccess) e = cudaMemcpy(P->d_hcols, hc.data(), hc.size() * sizeof(double), cudaMemcpyHostToDevice);
-    // factors slot-major on the device: lu[s * m + rank]
+    // factors slot-major on the device, rows ordered colour, level, column:
+    // lu[s * m + (c * P + j + 1) * (ncol / 4) + q] for rank (c * ncol/4 + q) * P + j + 1
     {
         std::vector<double> t((size_t)m * ns);
         std::vector<float> t32((size_t)m * ns);
-        for (long long i = 0; i < m; ++i)
+        const long long per = H.ncol / 4;
+        for (long long i = 0; i < m; ++i) {
+            const long long c = i / (per * H.P), rem = i % (per * H.P), q = rem / H.P, a = rem % H.P;
+            const long long i2 = (c * H.P + a) * per + q;
             for (int s = 0; s < ns; ++s) {
                 double v = lu_rows[(size_t)i * ns + s];
-                t[(size_t)s * m + i] = v;
-                t32[(size_t)s * m + i] = (float)v;
+                t[(size_t)s * m + i2] = v;
+                t32[(size_t)s * m + i2] = (float)v;
             }
+        }
         if (e == cudaSuccess) e = cudaMemcpy(P->d_lu64, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(P->d_lu32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
         std::vector<float> u32(udinv.size());
@@ -487,6 +527,8 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     D.h = P->d_hcols; D.hx = P->d_hcols + H.ncol; D.hy = P->d_hcols + 2 * H.ncol;
     D.hxx = P->d_hcols + 3 * H.ncol; D.hyy = P->d_hcols + 4 * H.ncol;
     D.gp = P->d_geom;
+    D.gp32 = P->d_geom32;
+    D.w32 = P->d_weights32;
     D.lu64 = P->d_lu64; D.lu32 = P->d_lu32; D.udinv64 = P->d_udinv64; D.udinv32 = P->d_udinv32;
     D.linv64 = P->d_linv64; D.uinv64 = P->d_uinv64; D.linv32 = P->d_linv32; D.uinv32 = P->d_uinv32;
     // algorithmic cost per point: 7-point sums counted as 7 fused multiply-adds (14 flops)

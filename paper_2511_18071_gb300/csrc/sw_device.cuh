@@ -94,8 +94,33 @@ __device__ inline void geometry_columns(const Dev &D, const double *eta_prev, co
             cc[CC_BY0 * n + c] = hy * e;
             cc[CC_BY1 * n + c] = dcy1 * e;
         }
+        if (D.gp32) {
+            const int nc = D.three_d ? NCC : CC_GN + 1;
+            for (int k = 0; k < nc; ++k) D.gp32[k * n + c] = (float)cc[k * n + c];
+        }
     }
 }
+
+// Weights and per-column coefficients in the arithmetic precision of the caller.
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+    __device__ static const double *wx1(const Dev &D) { return D.wx1; }
+    __device__ static const double *wx2(const Dev &D) { return D.wx2; }
+    __device__ static const double *wy1(const Dev &D) { return D.wy1; }
+    __device__ static const double *wy2(const Dev &D) { return D.wy2; }
+    __device__ static const double *ws1(const Dev &D) { return D.ws1; }
+    __device__ static const double *ws2(const Dev &D) { return D.ws2; }
+    __device__ static const double *cc(const Dev &D) { return D.gp; }
+};
+template <> struct Prec<float> {
+    __device__ static const float *wx1(const Dev &D) { return D.w32; }
+    __device__ static const float *wx2(const Dev &D) { return D.w32 + W; }
+    __device__ static const float *wy1(const Dev &D) { return D.w32 + 2 * W; }
+    __device__ static const float *wy2(const Dev &D) { return D.w32 + 3 * W; }
+    __device__ static const float *ws1(const Dev &D) { return D.w32 + 4 * W; }
+    __device__ static const float *ws2(const Dev &D) { return D.w32 + 4 * W + D.P * W; }
+    __device__ static const float *cc(const Dev &D) { return D.gp32; }
+};
 
 // ---------------------------------------------------------------------------
 // a2: matrix-free operator y = A(eta^(i-1), eta^(i)) p (Eq. 16-18).
@@ -135,19 +160,21 @@ __device__ inline void apply_tile(const Dev &D, const Tiling &tl, int tile, T *s
     }
     __syncthreads();
     // q = D_sigma p on tile + halo
+    const T *ws1 = Prec<T>::ws1(D), *ws2 = Prec<T>::ws2(D);
+    const T *wx1 = Prec<T>::wx1(D), *wx2 = Prec<T>::wx2(D), *wy1 = Prec<T>::wy1(D), *wy2 = Prec<T>::wy2(D);
     for (int idx = tid; idx < P * HW; idx += blockDim.x) {
         int l = idx / HW, r = idx - l * HW;
-        const double *w1 = D.ws1 + l * W;
+        const T *w1 = ws1 + l * W;
         int base = (D.win[l] + 1) * HW + r;
         T s = T(0);
 #pragma unroll
-        for (int k = 0; k < W; ++k) s += T(w1[k]) * sp[base + k * HW];
+        for (int k = 0; k < W; ++k) s += w1[k] * sp[base + k * HW];
         sq[idx] = s;
     }
     __syncthreads();
     const int n = D.ncol;
-    const T inv_nzm1 = T(1.0 / (D.nz - 1));
-    const double *cc = D.gp;
+    const T inv_nzm1 = T(1) / T(D.nz - 1);
+    const T *cc = Prec<T>::cc(D);
     for (int idx = tid; idx < P * tl.TX * tl.TY; idx += blockDim.x) {
         int l = idx / (tl.TX * tl.TY), r = idx - l * (tl.TX * tl.TY);
         int a = r % tl.TX + HALF, b = D.three_d ? r / tl.TX + HALF : 0;
@@ -163,47 +190,47 @@ __device__ inline void apply_tile(const Dev &D, const Tiling &tl, int tile, T *s
             T px = T(0), py = T(0);
 #pragma unroll
             for (int t = -HALF; t <= HALF; ++t) {
-                px += T(D.wx1[t + HALF]) * sp[HW + hr + t];
-                if (D.three_d) py += T(D.wy1[t + HALF]) * sp[HW + hr + t * HX];
+                px += wx1[t + HALF] * sp[HW + hr + t];
+                if (D.three_d) py += wy1[t + HALF] * sp[HW + hr + t * HX];
             }
-            y = T(cc[CC_GS * n + c]) * sq[HW + hr] + T(cc[CC_GX * n + c]) * px;
-            if (D.three_d) y += T(cc[CC_GY * n + c]) * py;
+            y = cc[CC_GS * n + c] * sq[HW + hr] + cc[CC_GX * n + c] * px;
+            if (D.three_d) y += cc[CC_GY * n + c] * py;
         } else {
             T sg = T(l - 1) * inv_nzm1;
-            T ap1 = T(cc[CC_AP1 * n + c]);
-            T aa = T(cc[CC_AP0 * n + c]) - sg * ap1;
-            T bb = T(cc[CC_BP0 * n + c]) - sg * T(cc[CC_BP1 * n + c]);
-            T ax = T(cc[CC_AXP0 * n + c]) - sg * T(cc[CC_AXP1 * n + c]) - aa * ap1;
+            T ap1 = cc[CC_AP1 * n + c];
+            T aa = cc[CC_AP0 * n + c] - sg * ap1;
+            T bb = cc[CC_BP0 * n + c] - sg * cc[CC_BP1 * n + c];
+            T ax = cc[CC_AXP0 * n + c] - sg * cc[CC_AXP1 * n + c] - aa * ap1;
             T c_xs = aa + bb;
-            T c_ss = aa * bb + T(cc[CC_EF * n + c]);
+            T c_ss = aa * bb + cc[CC_EF * n + c];
             T c_s = ax - bb * ap1;
             const T *pl = sp + l * HW + hr;
             const T *ql = sq + l * HW + hr;
             T pxx = T(0), pxs = T(0);
 #pragma unroll
             for (int t = -HALF; t <= HALF; ++t) {
-                pxx += T(D.wx2[t + HALF]) * pl[t];
-                pxs += T(D.wx1[t + HALF]) * ql[t];
+                pxx += wx2[t + HALF] * pl[t];
+                pxs += wx1[t + HALF] * ql[t];
             }
-            const double *w2 = D.ws2 + l * W;
+            const T *w2 = ws2 + l * W;
             const T *pc = sp + (D.win[l] + 1) * HW + hr;
             T pss = T(0);
 #pragma unroll
-            for (int k = 0; k < W; ++k) pss += T(w2[k]) * pc[k * HW];
+            for (int k = 0; k < W; ++k) pss += w2[k] * pc[k * HW];
             y = pxx + c_xs * pxs + c_s * ql[0];
             if (D.three_d) {
-                T ay1 = T(cc[CC_AY1 * n + c]);
-                T ay = T(cc[CC_AY0 * n + c]) - sg * ay1;
-                T by = T(cc[CC_BY0 * n + c]) - sg * T(cc[CC_BY1 * n + c]);
-                T ayy = T(cc[CC_AYY0 * n + c]) - sg * T(cc[CC_AYY1 * n + c]) - ay * ay1;
+                T ay1 = cc[CC_AY1 * n + c];
+                T ay = cc[CC_AY0 * n + c] - sg * ay1;
+                T by = cc[CC_BY0 * n + c] - sg * cc[CC_BY1 * n + c];
+                T ayy = cc[CC_AYY0 * n + c] - sg * cc[CC_AYY1 * n + c] - ay * ay1;
                 c_ss += ay * by;
                 T c_ys = ay + by;
                 T c_sy = ayy - by * ay1;
                 T pyy = T(0), pys = T(0);
 #pragma unroll
                 for (int t = -HALF; t <= HALF; ++t) {
-                    pyy += T(D.wy2[t + HALF]) * pl[t * HX];
-                    pys += T(D.wy1[t + HALF]) * ql[t * HX];
+                    pyy += wy2[t + HALF] * pl[t * HX];
+                    pys += wy1[t + HALF] * ql[t * HX];
                 }
                 y += pyy + c_ys * pys + c_sy * ql[0];
             }
@@ -303,6 +330,11 @@ template <> struct Off<BOX3D> {
     __device__ static constexpr int slot(int i) { return i < 42 ? (ox(i) + 3) * 7 + i % 7 : 49 + ((i - 42) / 7) * 7 + (i - 42) % 7; }
 };
 
+// Device row index of the factors: colour, level, column within the colour.
+__device__ __forceinline__ long long fac_row(const Dev &D, int c, int q, int j) {
+    return ((long long)c * D.P + (j + 1)) * (D.ncol >> 2) + q;
+}
+
 // sum over the off-column slots whose neighbour colour satisfies pick(colour)
 template <int L, typename T, bool LOWER>
 __device__ __forceinline__ T off_column_sum(const Dev &D, const T *lu, const T *vals, int c, int ix, int iy, int j,
@@ -367,7 +399,6 @@ __device__ inline void ilu_fwd_column_t(const Dev &D, int c, int q, const TI *in
     const int col = col_of(D, c, q);
     const int ix = col % D.nx, iy = col / D.nx;
     const long long cr = (long long)c * (D.ncol >> 2) + q;
-    const long long rbase = cr * D.P;
     T g[2], y[2];
     const int jl[2] = {lane - 1, lane + 31};
 #pragma unroll
@@ -376,7 +407,7 @@ __device__ inline void ilu_fwd_column_t(const Dev &D, int c, int q, const TI *in
         g[h] = T(0);
         if (j >= D.nz) continue;
         g[h] = T(in[(long long)(j + 1) * D.ncol + col]) -
-               off_column_sum<L, T, true>(D, lu, out, c, ix, iy, j, rbase + j + 1);
+               off_column_sum<L, T, true>(D, lu, out, c, ix, iy, j, fac_row(D, c, q, j));
     }
     // in-column part: y = (unit lower block)^-1 g
     column_block_product<T>(linv_ptr<T>(D) + cr * D.P * D.P, g, y, D.P, lane);
@@ -392,7 +423,6 @@ __device__ inline void ilu_bwd_column_t(const Dev &D, int c, int q, T *out, int 
     const int col = col_of(D, c, q);
     const int ix = col % D.nx, iy = col / D.nx;
     const long long cr = (long long)c * (D.ncol >> 2) + q;
-    const long long rbase = cr * D.P;
     T g[2], x[2];
     const int jl[2] = {lane - 1, lane + 31};
 #pragma unroll
@@ -401,7 +431,7 @@ __device__ inline void ilu_bwd_column_t(const Dev &D, int c, int q, T *out, int 
         g[h] = T(0);
         if (j >= D.nz) continue;
         g[h] = out[(long long)(j + 1) * D.ncol + col] -
-               off_column_sum<L, T, false>(D, lu, out, c, ix, iy, j, rbase + j + 1);
+               off_column_sum<L, T, false>(D, lu, out, c, ix, iy, j, fac_row(D, c, q, j));
     }
     __syncwarp();
     // in-column part: x = (upper block)^-1 g
@@ -409,6 +439,45 @@ __device__ inline void ilu_bwd_column_t(const Dev &D, int c, int q, T *out, int 
 #pragma unroll
     for (int h = 0; h < 2; ++h)
         if (jl[h] < D.nz) out[(long long)(jl[h] + 1) * D.ncol + col] = x[h];
+}
+
+// Two-phase sweep of one colour for large problems.  Phase 1, one thread per
+// row (consecutive threads take consecutive columns of one level, so factor
+// reads are coalesced): g = rhs - (couplings to the other colours), stored in
+// place.  Phase 2, one warp per column: the in-column block product.
+template <int L, typename T, typename TI, bool LOWER>
+__device__ inline void ilu_gather_row_t(const Dev &D, int c, long long row, const TI *in, T *out) {
+    const int per = D.ncol >> 2;
+    const int q = (int)(row % per), j = (int)(row / per) - 1;
+    const int col = col_of(D, c, q);
+    const int ix = col % D.nx, iy = col / D.nx;
+    const long long node = (long long)(j + 1) * D.ncol + col;
+    const T rhs = LOWER ? T(in[node]) : out[node];
+    out[node] = rhs - off_column_sum<L, T, LOWER>(D, lu_ptr<T>(D), out, c, ix, iy, j, fac_row(D, c, q, j));
+}
+template <typename T, typename TI, bool LOWER>
+__device__ inline void ilu_gather_row(const Dev &D, int c, long long row, const TI *in, T *out) {
+    switch (D.layout) {
+    case CROSS2D: ilu_gather_row_t<CROSS2D, T, TI, LOWER>(D, c, row, in, out); break;
+    case BOX2D: ilu_gather_row_t<BOX2D, T, TI, LOWER>(D, c, row, in, out); break;
+    case CROSS3D: ilu_gather_row_t<CROSS3D, T, TI, LOWER>(D, c, row, in, out); break;
+    default: ilu_gather_row_t<BOX3D, T, TI, LOWER>(D, c, row, in, out); break;
+    }
+}
+template <typename T>
+__device__ inline void ilu_column_product(const Dev &D, int c, int q, T *out, int lane, bool upper) {
+    const int col = col_of(D, c, q);
+    const long long cr = (long long)c * (D.ncol >> 2) + q;
+    T g[2], y[2];
+    const int jl[2] = {lane - 1, lane + 31};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) g[h] = jl[h] < D.nz ? out[(long long)(jl[h] + 1) * D.ncol + col] : T(0);
+    __syncwarp();
+    const T *blk = (upper ? uinv_ptr<T>(D) : linv_ptr<T>(D)) + cr * D.P * D.P;
+    column_block_product<T>(blk, g, y, D.P, lane);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (jl[h] < D.nz) out[(long long)(jl[h] + 1) * D.ncol + col] = y[h];
 }
 
 // runtime dispatch on the layout

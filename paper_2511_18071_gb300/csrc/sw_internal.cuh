@@ -41,6 +41,8 @@ struct Dev {
     const int *win;                        // P, first level of the sigma window of level j
     const double *h, *hx, *hy, *hxx, *hyy; // ncol
     double *gp;                            // per-column coefficients of the current geometry pair
+    float *gp32;                           // the same in FP32 (for the FP32 operator; may be null)
+    const float *w32;                      // weights in FP32: wx1, wx2, wy1, wy2 (7 each), ws1, ws2 (P x 7)
     const double *lu64;                    // nslot x m (rank-major), FP64 factors
     const float *lu32;                     // same, FP32 copy (mixed precision)
     const double *udinv64;                 // 1 / u_jj per rank
@@ -71,6 +73,8 @@ struct Problem {
     int *d_win = nullptr;
     double *d_hcols = nullptr;     // h, hx, hy, hxx, hyy
     double *d_geom = nullptr;      // per-column coefficients (20 x ncol)
+    float *d_geom32 = nullptr;     // FP32 copy (20 x ncol)
+    float *d_weights32 = nullptr;
     double *d_lu64 = nullptr, *d_udinv64 = nullptr;
     float *d_lu32 = nullptr, *d_udinv32 = nullptr;
     double *d_linv64 = nullptr, *d_uinv64 = nullptr;

@@ -58,6 +58,7 @@ struct SmemFixed {
     double cs[MAX_RESTART], sn[MAX_RESTART], g[MAX_RESTART + 1], y[MAX_RESTART];
     double scale[MAX_RESTART + 1];
     double hs[MAX_RESTART];   // projection coefficients of the current Gram-Schmidt pass, times scale
+    float hs32[MAX_RESTART];  // the same rounded to FP32 (FP32 inner form)
     double G[MAX_K * MAX_K], R1[MAX_K * MAX_K], R2[MAX_K * MAX_K], R[MAX_K * MAX_K];
     double c1[MAX_K], c2[MAX_K], z[MAX_K], tmp[MAX_K];
     int flags[8];
@@ -129,6 +130,22 @@ struct BlockTeam {
     }
 };
 
+// Compensated FP32 accumulation of products a*b (TwoProduct with fmaf, TwoSum;
+// Ogita, Rump & Oishi 2005): about twice FP32 precision, all on FP32 pipes.
+struct Dot2f {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = a * b;
+        const float ep = fmaf(a, b, -p);
+        const float t = s + p;
+        const float bp = t - s;
+        const float es = (s - (t - bp)) + (p - bp);
+        s = t;
+        c += es + ep;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // ---- loaders / stores for the tiled operator ----
 template <typename TV, typename TC>
 struct LdVec {
@@ -173,6 +190,26 @@ __device__ inline void team_ilu(Team &tm, const Dev &D, const TIn *in, TI *out) 
     const int gw = tm.bid * NWARPS + (threadIdx.x >> 5);
     const int nw = tm.nb * NWARPS;
     const int per = D.ncol >> 2;
+    if (per > 4 * nw) {
+        // large problem: row-parallel coupling gathers, then per-column products
+        const long long rows = (long long)per * D.P;
+        const long long tid = (long long)tm.bid * NTHREADS + threadIdx.x, nth = (long long)tm.nb * NTHREADS;
+        for (int c = 0; c < 4; ++c) {
+            for (long long r = tid; r < rows; r += nth) ilu_gather_row<TI, TIn, true>(D, c, r, in, out);
+            tm.sync();
+            for (int q = gw; q < per; q += nw) ilu_column_product<TI>(D, c, q, out, lane, false);
+            tm.sync();
+        }
+        for (int c = 3; c >= 0; --c) {
+            if (c < 3) {
+                for (long long r = tid; r < rows; r += nth) ilu_gather_row<TI, TI, false>(D, c, r, out, out);
+                tm.sync();
+            }
+            for (int q = gw; q < per; q += nw) ilu_column_product<TI>(D, c, q, out, lane, true);
+            tm.sync();
+        }
+        return;
+    }
     for (int c = 0; c < 4; ++c) {
         for (int q = gw; q < per; q += nw) ilu_fwd_column<TI, TIn>(D, c, q, in, out, lane);
         if (c < 3) tm.sync();
@@ -525,17 +562,39 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
                 double v[32];
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = 0.0;
-                for (long long kc = k0; 32 * kc < m; kc += kstep) {
-                    const long long p = 32 * kc + wlane;
-                    if (p >= m) continue;
-                    double vb[32];
+                if constexpr (sizeof(TI) == 4) {
+                    Dot2f acc[32];
+                    for (long long kc = k0; 32 * kc < m; kc += kstep) {
+                        const long long p = 32 * kc + wlane;
+                        if (p >= m) continue;
+                        float vb[32];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (double)V[(size_t)i * m + p] : 0.0;
-                    const double wv = (double)w[p];
+                        for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (float)V[(size_t)i * m + p] : 0.f;
+                        const float wv = (float)w[p];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            if (i > j) break;
+                            acc[i].add(vb[i], wv);
+                        }
+                    }
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         if (i > j) break;
-                        v[i] += vb[i] * wv;
+                        v[i] = acc[i].value();
+                    }
+                } else {
+                    for (long long kc = k0; 32 * kc < m; kc += kstep) {
+                        const long long p = 32 * kc + wlane;
+                        if (p >= m) continue;
+                        double vb[32];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (double)V[(size_t)i * m + p] : 0.0;
+                        const double wv = (double)w[p];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            if (i > j) break;
+                            v[i] += vb[i] * wv;
+                        }
                     }
                 }
                 tm.sum32(v, j + 1, S, S.res, wactive);
@@ -545,30 +604,57 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
                     const double hi = i <= j ? S.res[i] * S.scale[i] : 0.0;
                     if (i <= j) S.H[i * MAX_RESTART + j] = hi;
                     S.hs[i] = i <= j ? hi * S.scale[i] : 0.0;
+                    S.hs32[i] = (float)S.hs[i];
                 }
                 __syncthreads();
                 // pass 2: w -= V h ; d'_i = V_i . w
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = 0.0;
-                for (long long kc = k0; 32 * kc < m; kc += kstep) {
-                    const long long p = 32 * kc + wlane;
-                    if (p >= m) continue;
-                    double vb[32];
+                if constexpr (sizeof(TI) == 4) {
+                    Dot2f acc[32];
+                    for (long long kc = k0; 32 * kc < m; kc += kstep) {
+                        const long long p = 32 * kc + wlane;
+                        if (p >= m) continue;
+                        float vb[32];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (double)V[(size_t)i * m + p] : 0.0;
-                    double wv = (double)w[p];
+                        for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (float)V[(size_t)i * m + p] : 0.f;
+                        float wv = (float)w[p];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (i > j) break;
-                        wv -= S.hs[i] * vb[i];
+                        for (int i = 0; i < 32; ++i) {
+                            if (i > j) break;
+                            wv = fmaf(-S.hs32[i], vb[i], wv);
+                        }
+                        w[p] = TI(wv);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            if (i > j) break;
+                            acc[i].add(vb[i], wv);
+                        }
                     }
-                    const TI wt = TI(wv);
-                    w[p] = wt;
-                    wv = (double)wt;
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         if (i > j) break;
-                        v[i] += vb[i] * wv;
+                        v[i] = acc[i].value();
+                    }
+                } else {
+                    for (long long kc = k0; 32 * kc < m; kc += kstep) {
+                        const long long p = 32 * kc + wlane;
+                        if (p >= m) continue;
+                        double vb[32];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (double)V[(size_t)i * m + p] : 0.0;
+                        double wv = (double)w[p];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            if (i > j) break;
+                            wv -= S.hs[i] * vb[i];
+                        }
+                        w[p] = TI(wv);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            if (i > j) break;
+                            v[i] += vb[i] * wv;
+                        }
                     }
                 }
                 tm.sum32(v, j + 1, S, S.res, wactive);
@@ -578,27 +664,46 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
                     const double hi = i <= j ? S.res[i] * S.scale[i] : 0.0;
                     if (i <= j) S.H[i * MAX_RESTART + j] += hi;
                     S.hs[i] = i <= j ? hi * S.scale[i] : 0.0;
+                    S.hs32[i] = (float)S.hs[i];
                 }
                 __syncthreads();
                 // pass 3: w -= V h' ; ||w||^2
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = 0.0;
-                for (long long kc = k0; 32 * kc < m; kc += kstep) {
-                    const long long p = 32 * kc + wlane;
-                    if (p >= m) continue;
-                    double vb[32];
+                if constexpr (sizeof(TI) == 4) {
+                    Dot2f acc;
+                    for (long long kc = k0; 32 * kc < m; kc += kstep) {
+                        const long long p = 32 * kc + wlane;
+                        if (p >= m) continue;
+                        float vb[32];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (double)V[(size_t)i * m + p] : 0.0;
-                    double wv = (double)w[p];
+                        for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (float)V[(size_t)i * m + p] : 0.f;
+                        float wv = (float)w[p];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (i > j) break;
-                        wv -= S.hs[i] * vb[i];
+                        for (int i = 0; i < 32; ++i) {
+                            if (i > j) break;
+                            wv = fmaf(-S.hs32[i], vb[i], wv);
+                        }
+                        w[p] = TI(wv);
+                        acc.add(wv, wv);
                     }
-                    const TI wt = TI(wv);
-                    w[p] = wt;
-                    wv = (double)wt;
-                    v[0] += wv * wv;
+                    v[0] = acc.value();
+                } else {
+                    for (long long kc = k0; 32 * kc < m; kc += kstep) {
+                        const long long p = 32 * kc + wlane;
+                        if (p >= m) continue;
+                        double vb[32];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (double)V[(size_t)i * m + p] : 0.0;
+                        double wv = (double)w[p];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            if (i > j) break;
+                            wv -= S.hs[i] * vb[i];
+                        }
+                        w[p] = TI(wv);
+                        v[0] += wv * wv;
+                    }
                 }
                 tm.sum32(v, 1, S, S.res, wactive);
                 tick(PH_CGS3);

@@ -154,3 +154,22 @@ def state_arrays(wl):
     st["Kw"] = np.zeros_like(st["w"])
     st["Keta"] = np.zeros_like(st["eta"])
     return st
+
+
+def batch_members(n=512, seed=5, nxs=(128, 256, 512, 1024, 2048), nzs=(9, 17, 33)):
+    """Uneven 2-D members: nx, nz drawn uniformly, kh ~ U[0.5, 3], a/h ~ U[0.005, 0.08],
+    half flat-bottomed, half over a seeded periodic trapezoidal bar."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nx = int(rng.choice(nxs))
+        nz = int(rng.choice(nzs))
+        kh = float(rng.uniform(0.5, 3.0))
+        a = float(rng.uniform(0.005, 0.08))
+        if i % 2 == 0:
+            wl = airy_2d(nx=nx, nz=nz, kh=kh, a_over_h=a, steps=1)
+        else:
+            wl = periodic_bar_2d(nx=nx, nz=nz, kh=kh, a_over_h=a, seed=int(rng.integers(1 << 30)), steps=1)
+        wl["name"] = "member%03d_%s" % (i, wl["name"])
+        out.append(wl)
+    return out
