@@ -164,6 +164,16 @@ def reference_arm(args, rank):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def replica_value(local_ms, nsolves_per_rank, world, dist=None, device=None):
+    """Whole-job solves/s of independent replicas: the slowest rank's time bounds the job."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    return world * nsolves_per_rank / (total_ms / 1e3), total_ms
+
+
 def source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2511_18071_gb300", "csrc")
@@ -257,11 +267,7 @@ def gpu_arm(args, rank, world, local_rank):
     s1 = sw.get_stats(P.handle)
     ph1 = sw.get_phase_times(P.handle)
     nsolves = 5 * args.steps
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * nsolves / (total_ms / 1e3)
+    value, total_ms = replica_value(total_ms, nsolves, world, dist, dev)
     its = (s1["total_iterations"] - s0["total_iterations"]) / nsolves
     mflops = s1["model_flops"] - s0["model_flops"]
     mbytes = s1["model_bytes"] - s0["model_bytes"]
