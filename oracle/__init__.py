@@ -69,12 +69,26 @@ def lib():
         L.or_stage.argtypes = [vp, C.POINTER(Physics), C.c_int, dp, vp, dp, dp, dp, vp, dp, dp, dp,
                                C.POINTER(Stats)]
         L.or_stage.restype = C.c_int
+        L.or_xcoord.argtypes = [vp, C.c_int]
+        L.or_xcoord.restype = C.c_double
+        L.or_relax_weight.argtypes = [C.c_double]
+        L.or_relax_weight.restype = C.c_double
+        L.or_wavenumber.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.or_wavenumber.restype = C.c_double
+        L.or_relax.argtypes = [vp, C.POINTER(Relaxation), C.c_double, dp, dp, dp]
         _lib = L
     return _lib
 
 
 class Grid(C.Structure):
-    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double), ("ly", C.c_double)]
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double), ("ly", C.c_double),
+                ("walls", C.c_int)]
+
+
+class Relaxation(C.Structure):
+    _fields_ = [("gen_x0", C.c_double), ("gen_x1", C.c_double), ("abs_x0", C.c_double), ("abs_x1", C.c_double),
+                ("height", C.c_double), ("period", C.c_double), ("depth", C.c_double), ("ramp_time", C.c_double),
+                ("g", C.c_double)]
 
 
 class Params(C.Structure):
@@ -135,6 +149,14 @@ def lstsq_qr(W, b):
     return z, rank
 
 
+def relax_weight(xi):
+    return lib().or_relax_weight(float(xi))
+
+
+def wavenumber(omega, depth, g=9.81):
+    return lib().or_wavenumber(float(omega), float(depth), float(g))
+
+
 def lserk45():
     a, b, c = np.zeros(5), np.zeros(5), np.zeros(5)
     lib().or_lserk45(a, b, c)
@@ -145,8 +167,9 @@ class OracleProblem:
     """One sigma-grid problem: operator, ILU(0), GMRES, EWMA history, stage driver."""
 
     def __init__(self, nx, ny, nz, lx, ly, h, restart=20, max_restarts=50, tol=1e-8, guess="cold", k=10,
-                 decay=0.9, n_init_solves=30, seed=2511):
-        self.grid = Grid(nx, ny, nz, lx, ly if ny > 1 else 0.0)
+                 decay=0.9, n_init_solves=30, seed=2511, walls=False):
+        self.grid = Grid(nx, ny, nz, lx, ly if ny > 1 else 0.0, int(bool(walls)))
+        self.walls = bool(walls)
         self.params = Params(restart, max_restarts, tol, GUESS[guess], k, decay, n_init_solves, seed)
         st = C.c_int(0)
         h = _f64(h).ravel()
@@ -275,3 +298,12 @@ class OracleProblem:
                               state["eta"], state["Ku"], _ptr(state.get("Kv")), state["Kw"], state["Keta"], p,
                               C.byref(st))
         return p, st.as_dict(), code
+
+    def xcoord(self):
+        """x of every column (walls: the ghost columns lie one spacing outside [0, lx])."""
+        return np.array([lib().or_xcoord(self._p, i) for i in range(self.nx)])
+
+    def relax(self, relaxation, t, state):
+        """Blend eta, u, w of ``state`` towards the zone targets at time t, in place (2-D)."""
+        rl = relaxation if isinstance(relaxation, Relaxation) else Relaxation(**relaxation)
+        lib().or_relax(self._p, C.byref(rl), float(t), state["u"], state["w"], state["eta"])

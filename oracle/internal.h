@@ -11,6 +11,7 @@ struct or_problem {
     int box;             /* structural pattern includes the sigma-cross terms */
     double dx, dy;
     double wx1[OR_W], wx2[OR_W], wy1[OR_W], wy2[OR_W];  /* centred periodic weights */
+    double wxo1[OR_W][OR_W], wxo2[OR_W][OR_W];          /* walls: weights at node o of a 7-node window */
     double *ws1, *ws2;   /* (nz+1) x 7 sigma weights, row j+1 */
     int *win;            /* (nz+1) first window level, row j+1 */
     double *h, *hx, *hy, *hxx, *hyy;  /* bathymetry and its surface-grid derivatives */
@@ -36,8 +37,16 @@ void or_colgeom_eval(const or_problem *P, const double *eta, or_colgeom *G);
 /* Periodic surface-grid derivatives D_chi, D_chichi, D_gamma, D_gammagamma (Sec. 3). */
 void or_surface_derivs(const or_problem *P, const double *f, double *fx, double *fy,
                        double *fxx, double *fyy);
-/* 3-D field derivatives at all nodes. */
-void or_field_dx(const or_problem *P, const double *f, double *out);
+/* The 7 columns and weights of the x derivatives at column ix.  Periodic: the
+ * centred window.  Walls: field != 0 selects the window of an unknown of the
+ * linear system (ghost columns included, start clamp(ix-3, 0, nx-7));
+ * field == 0 the window of surface data and velocities (physical columns
+ * only, start clamp(ix'-3, 1, nx-8) with ix' = ix moved off a ghost column). */
+void or_xwin(const or_problem *P, int ix, int field, int *cols, const double **w1, const double **w2);
+/* 1 for the ghost columns outside the walls. */
+int or_is_wall_ghost(const or_problem *P, int ix);
+/* 3-D field derivatives at all nodes (field: as in or_xwin). */
+void or_field_dx(const or_problem *P, const double *f, double *out, int field);
 void or_field_dy(const or_problem *P, const double *f, double *out);
 void or_field_dsigma(const or_problem *P, const double *f, double *out);
 void or_csr_free(or_csr *A);

@@ -6,6 +6,16 @@
  * sigma levels sigma_j = j/(nz-1), j = 0..nz-1, plus one ghost level j = -1
  * below the bed.  Node (ix, iy, j) has index ((j+1)*ny + iy)*nx + ix.
  *
+ * Walls (2-D, Sec. 5.1 and the flume of Sec. 5.3): the impermeable walls at
+ * x = 0 and x = lx carry the Neumann condition n . grad p = n . G through one
+ * ghost column outside each wall (columns 0 and nx-1).  The row of ghost node
+ * (0, j) is the wall condition n . grad^(i-1) p = n . G evaluated at the wall
+ * node (1, j), for j = -1..nz-2 (at j = -1 the condition is continued to the
+ * ghost level below the bed, which closes the corner); the surface node of a
+ * ghost column is a Dirichlet row like every surface node.  Next to a wall the
+ * 7-point x stencils are shifted inside [0, nx-1] (off-centred, as next to bed
+ * and surface in sigma).
+ *
  * Rows (Eq. 16-18):
  *   j = nz-1  free surface, homogeneous Dirichlet p = 0: the row is the identity;
  *   0 <= j <= nz-2  the mixed-stage operator grad^(i) . grad^(i-1) p, with the
@@ -39,6 +49,39 @@ static int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
 
 double or_sigma(const or_problem *P, int j) { return (double)j / (double)(P->g.nz - 1); }
 
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int or_is_wall_ghost(const or_problem *P, int ix)
+{
+    return P->g.walls && (ix == 0 || ix == P->g.nx - 1);
+}
+
+double or_xcoord(const or_problem *P, int ix)
+{
+    return P->g.walls ? (ix - 1) * P->dx : ix * P->dx;
+}
+
+void or_xwin(const or_problem *P, int ix, int field, int *cols, const double **w1, const double **w2)
+{
+    int nx = P->g.nx;
+    if (!P->g.walls) {
+        for (int t = 0; t < OR_W; ++t) cols[t] = wrap(ix + t - OR_HALF, nx);
+        *w1 = P->wx1;
+        *w2 = P->wx2;
+        return;
+    }
+    int s;
+    if (field) {
+        s = clampi(ix - OR_HALF, 0, nx - OR_W);
+    } else {
+        ix = clampi(ix, 1, nx - 2);
+        s = clampi(ix - OR_HALF, 1, nx - 1 - OR_W);
+    }
+    for (int t = 0; t < OR_W; ++t) cols[t] = s + t;
+    *w1 = P->wxo1[ix - s];
+    *w2 = P->wxo2[ix - s];
+}
+
 void or_csr_free(or_csr *A)
 {
     free(A->rowptr); free(A->col); free(A->val);
@@ -54,10 +97,13 @@ void or_surface_derivs(const or_problem *P, const double *f, double *fx, double 
     for (int iy = 0; iy < g->ny; ++iy)
         for (int ix = 0; ix < g->nx; ++ix) {
             double s1 = 0, s2 = 0, t1 = 0, t2 = 0;
+            int cols[OR_W];
+            const double *w1, *w2;
+            or_xwin(P, ix, 0, cols, &w1, &w2);
             for (int t = -OR_HALF; t <= OR_HALF; ++t) {
-                double vx = f[iy * g->nx + wrap(ix + t, g->nx)];
-                s1 += P->wx1[t + OR_HALF] * vx;
-                s2 += P->wx2[t + OR_HALF] * vx;
+                double vx = f[iy * g->nx + cols[t + OR_HALF]];
+                s1 += w1[t + OR_HALF] * vx;
+                s2 += w2[t + OR_HALF] * vx;
                 if (g->ny > 1) {
                     double vy = f[wrap(iy + t, g->ny) * g->nx + ix];
                     t1 += P->wy1[t + OR_HALF] * vy;
@@ -72,15 +118,17 @@ void or_surface_derivs(const or_problem *P, const double *f, double *fx, double 
         }
 }
 
-void or_field_dx(const or_problem *P, const double *f, double *out)
+void or_field_dx(const or_problem *P, const double *f, double *out, int field)
 {
     const or_grid *g = &P->g;
     for (int j = -1; j < g->nz; ++j)
         for (int iy = 0; iy < g->ny; ++iy)
             for (int ix = 0; ix < g->nx; ++ix) {
+                int cols[OR_W];
+                const double *w1, *w2;
+                or_xwin(P, ix, field, cols, &w1, &w2);
                 double s = 0;
-                for (int t = -OR_HALF; t <= OR_HALF; ++t)
-                    s += P->wx1[t + OR_HALF] * f[or_index(g, wrap(ix + t, g->nx), iy, j)];
+                for (int t = 0; t < OR_W; ++t) s += w1[t] * f[or_index(g, cols[t], iy, j)];
                 out[or_index(g, ix, iy, j)] = s;
             }
 }
@@ -183,6 +231,23 @@ static void build_row(const or_problem *P, const or_colgeom *Gp, const or_colgeo
         add(r, or_index(g, ix, iy, j), 1.0);
         return;
     }
+    int xc[OR_W];
+    const double *wx1, *wx2;
+    if (or_is_wall_ghost(P, ix)) {        /* wall row: n . grad^(i-1) p at the wall node (iw, j) */
+        int iw = ix == 0 ? 1 : g->nx - 2;
+        double nxs = ix == 0 ? -1.0 : 1.0;   /* outward normal (-1, 0) at x = 0, (1, 0) at x = lx */
+        int cw = iy * g->nx + iw;
+        or_xwin(P, iw, 1, xc, &wx1, &wx2);
+        for (int t = 0; t < OR_W; ++t) add(r, or_index(g, xc[t], iy, j), nxs * wx1[t]);
+        if (box) {
+            double a = (P->hx[cw] - or_sigma(P, j) * Gp->dx[cw]) / Gp->d[cw];   /* sigma_x^(i-1) */
+            int s0 = P->win[j + 1];
+            const double *w1s = P->ws1 + (j + 1) * OR_W;
+            for (int k = 0; k < OR_W; ++k) add(r, or_index(g, iw, iy, s0 + k), nxs * a * w1s[k]);
+        }
+        return;
+    }
+    or_xwin(P, ix, 1, xc, &wx1, &wx2);
     double hx = P->hx[c], hy = P->hy[c];
     if (j == -1) {                        /* ghost row: n . grad^(i-1) p at the bed */
         int jb = 0, s0 = P->win[jb + 1];
@@ -196,7 +261,7 @@ static void build_row(const or_problem *P, const or_colgeom *Gp, const or_colgeo
         for (int k = 0; k < OR_W; ++k) add(r, or_index(g, ix, iy, s0 + k), cs * w1s[k]);
         if (box) {
             for (int t = -OR_HALF; t <= OR_HALF; ++t) {
-                add(r, or_index(g, wrap(ix + t, g->nx), iy, jb), -nrm * hx * P->wx1[t + OR_HALF]);
+                add(r, or_index(g, xc[t + OR_HALF], iy, jb), -nrm * hx * wx1[t + OR_HALF]);
                 if (three_d)
                     add(r, or_index(g, ix, wrap(iy + t, g->ny), jb), -nrm * hy * P->wy1[t + OR_HALF]);
             }
@@ -225,7 +290,7 @@ static void build_row(const or_problem *P, const or_colgeom *Gp, const or_colgeo
     double c_s = ax + b * as + ayy + by_ * ays;
     double c_xs = a + b, c_ys = ay_ + by_;
     for (int t = -OR_HALF; t <= OR_HALF; ++t) {
-        add(r, or_index(g, wrap(ix + t, g->nx), iy, j), P->wx2[t + OR_HALF]);
+        add(r, or_index(g, xc[t + OR_HALF], iy, j), wx2[t + OR_HALF]);
         if (three_d) add(r, or_index(g, ix, wrap(iy + t, g->ny), j), P->wy2[t + OR_HALF]);
     }
     for (int k = 0; k < OR_W; ++k)
@@ -233,8 +298,8 @@ static void build_row(const or_problem *P, const or_colgeom *Gp, const or_colgeo
     if (box) {
         for (int t = -OR_HALF; t <= OR_HALF; ++t)
             for (int k = 0; k < OR_W; ++k) {
-                add(r, or_index(g, wrap(ix + t, g->nx), iy, s0 + k),
-                    c_xs * P->wx1[t + OR_HALF] * w1s[k]);
+                add(r, or_index(g, xc[t + OR_HALF], iy, s0 + k),
+                    c_xs * wx1[t + OR_HALF] * w1s[k]);
                 if (three_d)
                     add(r, or_index(g, ix, wrap(iy + t, g->ny), s0 + k),
                         c_ys * P->wy1[t + OR_HALF] * w1s[k]);
@@ -312,19 +377,26 @@ or_problem *or_create(const or_grid *g, const or_params *p, const double *h, int
     *status = OR_BAD_ARG;
     if (g->nx < 1 || g->ny < 1 || g->nz < OR_W || !(g->lx > 0) || (g->ny > 1 && !(g->ly > 0)))
         return NULL;
+    if (g->walls && (g->ny != 1 || g->nx < 16)) return NULL;
     if (p->restart < 1 || p->k < 0 || p->max_restarts < 0) return NULL;
     or_problem *P = calloc(1, sizeof(or_problem));
     P->g = *g;
     P->p = *p;
     P->ncol = g->nx * g->ny;
     P->m = P->ncol * (g->nz + 1);
-    P->dx = g->lx / g->nx;
+    P->dx = g->walls ? g->lx / (g->nx - 3) : g->lx / g->nx;
     P->dy = g->ny > 1 ? g->ly / g->ny : 1.0;
     /* centred periodic weights on offsets -3..3 */
     double xs[OR_W], cw[3 * OR_W];
     for (int t = 0; t < OR_W; ++t) xs[t] = (t - OR_HALF) * P->dx;
     or_fornberg(0.0, xs, OR_W, 2, cw);
     for (int t = 0; t < OR_W; ++t) { P->wx1[t] = cw[OR_W + t]; P->wx2[t] = cw[2 * OR_W + t]; }
+    /* walls: the 7 evaluation points of a window of 7 equispaced nodes */
+    for (int t = 0; t < OR_W; ++t) xs[t] = t * P->dx;
+    for (int o = 0; o < OR_W; ++o) {
+        or_fornberg(o * P->dx, xs, OR_W, 2, cw);
+        for (int t = 0; t < OR_W; ++t) { P->wxo1[o][t] = cw[OR_W + t]; P->wxo2[o][t] = cw[2 * OR_W + t]; }
+    }
     for (int t = 0; t < OR_W; ++t) xs[t] = (t - OR_HALF) * P->dy;
     or_fornberg(0.0, xs, OR_W, 2, cw);
     for (int t = 0; t < OR_W; ++t) { P->wy1[t] = cw[OR_W + t]; P->wy2[t] = cw[2 * OR_W + t]; }
@@ -373,12 +445,28 @@ or_problem *or_create(const or_grid *g, const or_params *p, const double *h, int
      * of four. */
     int *order = malloc(P->m * sizeof(int));
     int q = 0;
-    for (int col = 0; col < 4; ++col)
-        for (int iy = 0; iy < g->ny; ++iy)
-            for (int ix = 0; ix < g->nx; ++ix) {
-                if ((ix + iy) % 4 != col) continue;
-                for (int j = -1; j < g->nz; ++j) order[q++] = (int)or_index(g, ix, iy, j);
+    if (!g->walls) {
+        for (int col = 0; col < 4; ++col)
+            for (int iy = 0; iy < g->ny; ++iy)
+                for (int ix = 0; ix < g->nx; ++ix) {
+                    if ((ix + iy) % 4 != col) continue;
+                    for (int j = -1; j < g->nz; ++j) order[q++] = (int)or_index(g, ix, iy, j);
+                }
+    } else {
+        /* With walls the rows of columns 0-2 (and nx-3..nx-1) reach 7 columns
+         * inwards, so those six columns get three groups of their own after the
+         * four colours of columns 3..nx-4: {0, nx-1}, {1, nx-2}, {2, nx-3}. */
+        for (int col = 0; col < 4; ++col)
+            for (int ix = 3; ix <= g->nx - 4; ++ix) {
+                if (ix % 4 != col) continue;
+                for (int j = -1; j < g->nz; ++j) order[q++] = (int)or_index(g, ix, 0, j);
             }
+        for (int e = 0; e < 3; ++e) {
+            int pair[2] = {e, g->nx - 1 - e};
+            for (int u = 0; u < 2; ++u)
+                for (int j = -1; j < g->nz; ++j) order[q++] = (int)or_index(g, pair[u], 0, j);
+        }
+    }
     int st = or_build_ilu(P, order);
     free(order);
     if (st != OR_OK) { or_destroy(P); *status = st; return NULL; }

@@ -36,7 +36,10 @@ enum { OR_GUESS_COLD = 0, OR_GUESS_PREV = 1, OR_GUESS_EWMA = 2 };
 
 typedef struct {
     int nx, ny, nz;   /* columns in x and y (ny = 1 in 2D), sigma levels 0..nz-1 (ghost level -1 extra) */
-    double lx, ly;    /* periodic lengths in x and y */
+    double lx, ly;    /* periodic lengths in x and y; with walls, lx is the wall-to-wall length */
+    int walls;        /* 0: periodic in x.  1 (2-D only): vertical walls at x = 0 and x = lx, with
+                         columns 0 and nx-1 the ghost columns outside them (Sec. 5.1, Sec. 5.3):
+                         physical columns 1..nx-2 sit at x = (ix-1) lx/(nx-3) */
 } or_grid;
 
 typedef struct {
@@ -65,6 +68,9 @@ typedef struct {
 void or_fornberg(double z, const double *x, int n, int mmax, double *c);
 /* First sigma level of the 7-node window used at level j (j = -1..nz-1). */
 int or_sigma_window(int nz, int j);
+/* x coordinate of column ix (periodic: ix lx/nx; walls: (ix-1) lx/(nx-3)). */
+typedef struct or_problem or_problem;
+double or_xcoord(const or_problem *P, int ix);
 
 /* ---- operator (operator.c) ---- */
 typedef struct {
@@ -72,8 +78,6 @@ typedef struct {
     int *rowptr, *col;
     double *val;
 } or_csr;
-
-typedef struct or_problem or_problem;
 
 /* Node index of (ix, iy, j), j = -1 (ghost) .. nz-1 (surface); x fastest, ghost plane first. */
 long or_index(const or_grid *g, int ix, int iy, int j);
@@ -137,6 +141,24 @@ void or_rhs(const or_problem *P, const or_physics *ph, int stage,
 int or_stage(or_problem *P, const or_physics *ph, int stage,
              double *u, double *v, double *w, double *eta,
              double *Ku, double *Kv, double *Kw, double *Keta, double *p, or_stats *st);
+
+/* ---- wave generation and absorption zones (physics.c, Sec. 5.3) ---- */
+typedef struct {
+    double gen_x0, gen_x1;   /* generation zone [gen_x0, gen_x1] (empty when gen_x1 <= gen_x0) */
+    double abs_x0, abs_x1;   /* absorption zone [abs_x0, abs_x1] (empty when abs_x1 <= abs_x0) */
+    double height, period;   /* incident linear wave: height H and period T */
+    double depth;            /* still-water depth the incident wave is computed for */
+    double ramp_time;        /* the incident amplitude ramps up smoothly over [0, ramp_time] */
+    double g;
+} or_relaxation;
+
+/* Relaxation weight Gamma(xi) = 1 - (exp(xi^3.5) - 1)/(e - 1): 1 at the inner end of a zone
+ * (xi = 0), 0 at its outer end (xi = 1). */
+double or_relax_weight(double xi);
+/* Wavenumber k of the linear dispersion relation omega^2 = g k tanh(k depth) (Newton). */
+double or_wavenumber(double omega, double depth, double g);
+/* phi <- Gamma phi + (1 - Gamma) phi_target for eta, then u and w (2-D), at time t. */
+void or_relax(const or_problem *P, const or_relaxation *rl, double t, double *u, double *w, double *eta);
 
 #ifdef __cplusplus
 }

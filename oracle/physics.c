@@ -12,6 +12,20 @@
  *       + rho (sigma/d^(i-1)) (D_tau eta^(i-1)) D_sigma u
  * the interior rows take grad^(i) . G, the ghost rows n . G at the bed node,
  * and the surface rows 0.  D_tau eta^(i-1) is f_eta of Eq. (14b) at stage i-1.
+ *
+ * Walls: the ghost-column rows take n . G at the wall node; x derivatives of
+ * the velocities and of G use the physical columns only, those of p the
+ * ghost columns too.  The ghost columns carry no flow: f_eta and f_u are zero
+ * there, so their state never changes.
+ *
+ * Generation and absorption zones (Sec. 5.3): after each stage the surface
+ * and the velocities inside a zone are blended towards a target,
+ * phi <- Gamma phi + (1 - Gamma) phi_target, with the relaxation weight of
+ * Engsig-Karup, Bingham & Lindberg (J. Comput. Phys. 228, 2009),
+ * Gamma(xi) = 1 - (exp(xi^3.5) - 1)/(e - 1), xi = 0 at the inner end of the
+ * zone and 1 at the wall.  The generation target is the incident linear
+ * (Airy) wave of height H and period T, its amplitude ramped in time by
+ * (1 - cos(pi t / t_ramp))/2; the absorption target is still water.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -53,7 +67,7 @@ void or_f_eta(const or_problem *P, const double *u, const double *v, const doubl
         for (int ix = 0; ix < g->nx; ++ix) {
             int c = iy * g->nx + ix;
             long s = or_index(g, ix, iy, g->nz - 1);
-            out[c] = w[s] - u[s] * ex[c] - (v ? v[s] * ey[c] : 0.0);
+            out[c] = or_is_wall_ghost(P, ix) ? 0.0 : w[s] - u[s] * ex[c] - (v ? v[s] * ey[c] : 0.0);
         }
     free(ex); free(ey);
 }
@@ -76,7 +90,7 @@ static void advect(const or_problem *P, const or_colgeom *Gp, const double *u, c
     const or_grid *g = &P->g;
     int m = P->m;
     double *px = malloc(m * sizeof(double)), *py = malloc(m * sizeof(double));
-    or_field_dx(P, phi, px);
+    or_field_dx(P, phi, px, 0);
     or_field_dy(P, phi, py);
     or_field_dsigma(P, phi, dphis);
     for (int j = -1; j < g->nz; ++j)
@@ -130,7 +144,7 @@ void or_rhs(const or_problem *P, const or_physics *ph, int stage,
     double *gxu = malloc(m * sizeof(double)), *gsu = malloc(m * sizeof(double));
     double *gyv = malloc(m * sizeof(double)), *gsv = malloc(m * sizeof(double));
     double *gsw = malloc(m * sizeof(double));
-    or_field_dx(P, G[0], gxu); or_field_dsigma(P, G[0], gsu);
+    or_field_dx(P, G[0], gxu, 0); or_field_dsigma(P, G[0], gsu);
     or_field_dy(P, G[1], gyv); or_field_dsigma(P, G[1], gsv);
     or_field_dsigma(P, G[2], gsw);
     for (int j = -1; j < g->nz; ++j)
@@ -139,6 +153,12 @@ void or_rhs(const or_problem *P, const or_physics *ph, int stage,
                 long q = or_index(g, ix, iy, j);
                 int c = iy * g->nx + ix;
                 if (j == g->nz - 1) { b[q] = 0.0; continue; }
+                if (or_is_wall_ghost(P, ix)) {          /* n . G at the wall node */
+                    int iw = ix == 0 ? 1 : g->nx - 2;
+                    double nxs = ix == 0 ? -1.0 : 1.0;
+                    b[q] = nxs * G[0][or_index(g, iw, iy, j)];
+                    continue;
+                }
                 if (j == -1) {
                     long qb = or_index(g, ix, iy, 0);
                     double hx = P->hx[c], hy = P->hy[c];
@@ -181,7 +201,7 @@ int or_stage(or_problem *P, const or_physics *ph, int stage,
     or_colgeom_eval(P, eta, &Gp);
     double *px = malloc(m * sizeof(double)), *py = malloc(m * sizeof(double));
     double *ps = malloc(m * sizeof(double));
-    or_field_dx(P, p, px); or_field_dy(P, p, py); or_field_dsigma(P, p, ps);
+    or_field_dx(P, p, px, 1); or_field_dy(P, p, py); or_field_dsigma(P, p, ps);
     double *comp[3] = {u, v, w};
     double *Kc[3] = {Ku, Kv, Kw};
     double *adv[3], *ds[3];
@@ -203,6 +223,7 @@ int or_stage(or_problem *P, const or_physics *ph, int stage,
                     double Fd = d == 2 ? -ph->g : 0.0;
                     double fu = -gradp[d] / ph->rho + Fd - adv[d][q]
                                 + (sg / Gp.d[c]) * feta[c] * ds[d][q];
+                    if (or_is_wall_ghost(P, ix)) fu = 0.0;
                     Kc[d][q] = a_i * Kc[d][q] + dt * fu;
                 }
             }
@@ -214,4 +235,68 @@ int or_stage(or_problem *P, const or_physics *ph, int stage,
     or_colgeom_free(&Gp);
     free(feta); free(eta_new); free(b); free(px); free(py); free(ps);
     return status;
+}
+
+/* ---------- generation and absorption zones ---------- */
+
+double or_relax_weight(double xi)
+{
+    if (xi <= 0.0) return 1.0;
+    if (xi >= 1.0) return 0.0;
+    return 1.0 - (exp(pow(xi, 3.5)) - 1.0) / (exp(1.0) - 1.0);
+}
+
+double or_wavenumber(double omega, double depth, double g)
+{
+    double k = omega * omega / g;            /* deep-water start; F is increasing and concave */
+    for (int it = 0; it < 100; ++it) {
+        double th = tanh(k * depth);
+        double F = g * k * th - omega * omega;
+        double dF = g * th + g * k * depth * (1.0 - th * th);
+        double dk = F / dF;
+        k -= dk;
+        if (fabs(dk) <= 1e-15 * k) break;
+    }
+    return k;
+}
+
+void or_relax(const or_problem *P, const or_relaxation *rl, double t, double *u, double *w, double *eta)
+{
+    const or_grid *g = &P->g;
+    const double pi = 3.14159265358979323846;
+    double omega = 2.0 * pi / rl->period;
+    double k = or_wavenumber(omega, rl->depth, rl->g);
+    double ramp = 1.0;
+    if (rl->ramp_time > 0.0 && t < rl->ramp_time) ramp = 0.5 * (1.0 - cos(pi * t / rl->ramp_time));
+    double amp = 0.5 * rl->height * ramp;
+    for (int ix = 0; ix < g->nx; ++ix) {
+        if (or_is_wall_ghost(P, ix)) continue;
+        double x = or_xcoord(P, ix);
+        double gam, th = k * x - omega * t;
+        int gen;
+        if (rl->gen_x1 > rl->gen_x0 && x >= rl->gen_x0 && x <= rl->gen_x1) {
+            gam = or_relax_weight((rl->gen_x1 - x) / (rl->gen_x1 - rl->gen_x0));
+            gen = 1;
+        } else if (rl->abs_x1 > rl->abs_x0 && x >= rl->abs_x0 && x <= rl->abs_x1) {
+            gam = or_relax_weight((x - rl->abs_x0) / (rl->abs_x1 - rl->abs_x0));
+            gen = 0;
+        } else {
+            continue;
+        }
+        double eta_t = gen ? amp * cos(th) : 0.0;
+        eta[ix] = gam * eta[ix] + (1.0 - gam) * eta_t;
+        double d = P->h[ix] + eta[ix];
+        for (int j = -1; j < g->nz; ++j) {
+            long q = or_index(g, ix, 0, j);
+            double z = or_sigma(P, j) * d - P->h[ix];
+            double ut = 0.0, wt = 0.0;
+            if (gen) {
+                double sh = sinh(k * rl->depth);
+                ut = amp * omega * cosh(k * (z + rl->depth)) / sh * cos(th);
+                wt = amp * omega * sinh(k * (z + rl->depth)) / sh * sin(th);
+            }
+            u[q] = gam * u[q] + (1.0 - gam) * ut;
+            w[q] = gam * w[q] + (1.0 - gam) * wt;
+        }
+    }
 }

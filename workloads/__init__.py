@@ -173,3 +173,77 @@ def batch_members(n=512, seed=5, nxs=(128, 256, 512, 1024, 2048), nzs=(9, 17, 33
         wl["name"] = "member%03d_%s" % (i, wl["name"])
         out.append(wl)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Wave flume with walls: ghost columns 0 and nx-1 lie one spacing outside the
+# walls at x = 0 and x = lx; physical columns 1..nx-2 at x = (ix-1) lx/(nx-3).
+# ---------------------------------------------------------------------------
+def wall_x(nx, lx):
+    return (np.arange(nx) - 1.0) * (lx / (nx - 3))
+
+
+def linear_wavenumber(omega, depth):
+    k = omega * omega / G
+    for _ in range(100):
+        th = math.tanh(k * depth)
+        dk = (G * k * th - omega * omega) / (G * th + G * k * depth * (1 - th * th))
+        k -= dk
+        if abs(dk) <= 1e-15 * k:
+            break
+    return k
+
+
+def beji_bar_depth(x):
+    """Trapezoidal submerged bar: 0.4 m, 1:20 up to 0.1 m over [6, 12], flat to 14, 1:10 down to 0.4 at 17."""
+    h = np.full_like(x, 0.4)
+    up = (x >= 6) & (x < 12)
+    h[up] = 0.4 - (x[up] - 6) / 20
+    h[(x >= 12) & (x < 14)] = 0.1
+    dn = (x >= 14) & (x < 17)
+    h[dn] = 0.1 + (x[dn] - 14) / 10
+    return h
+
+
+def flume_2d(nx=2048, nz=17, lx=40.0, depth="bar", height=0.02, period=2.02, gen=(0.0, 3.0), absorb=None,
+             ramp_periods=2.0, steps=4000, cr=0.5):
+    """Wave flume between walls, starting from rest; waves enter through a
+    relaxation generation zone and leave through an absorption zone.
+
+    depth: "bar" for the trapezoidal bar (0.4 m still-water depth away from it)
+    or a number for a flat bed.  The time step has Courant number cr for the
+    phase speed of the incident wave in 0.4 m (or the flat depth).
+    """
+    x = wall_x(nx, lx)
+    h0 = 0.4 if depth == "bar" else float(depth)
+    if depth == "bar":
+        h = beji_bar_depth(np.clip(x, 0.0, lx))
+    else:
+        h = np.full(nx, h0)
+    h[0], h[-1] = h[1], h[-2]
+    if absorb is None:
+        absorb = (lx - 4.0, lx)
+    om = 2 * math.pi / period
+    k = linear_wavenumber(om, h0)
+    dx = lx / (nx - 3)
+    dt = cr * dx / (om / k)
+    m = nx * (nz + 1)
+    relax = dict(gen_x0=gen[0], gen_x1=gen[1], abs_x0=absorb[0], abs_x1=absorb[1], height=height, period=period,
+                 depth=h0, ramp_time=ramp_periods * period, g=G)
+    return dict(name="flume2d_%dx%d_%s" % (nx, nz, "bar" if depth == "bar" else "flat"), nx=nx, ny=1, nz=nz,
+                lx=lx, ly=0.0, h=h, eta=np.zeros(nx), u=np.zeros(m), v=None, w=np.zeros(m), dt=dt, steps=steps,
+                g=G, rho=RHO, m=m, walls=True, relax=relax, k=k, omega=om)
+
+
+def standing_wave_basin(nx=67, nz=9, depth=1.0, kh=1.0, a_over_h=0.01, steps=128):
+    """Closed basin one wavelength long, free surface a cos(k x) at rest (a standing wave at its crest)."""
+    k = kh / depth
+    lx = 2 * math.pi / k
+    x = wall_x(nx, lx)
+    h = np.full(nx, depth)
+    m = nx * (nz + 1)
+    om = dispersion_omega(k, depth)
+    T = 2 * math.pi / om
+    return dict(name="basin2d_%dx%d" % (nx, nz), nx=nx, ny=1, nz=nz, lx=lx, ly=0.0, h=h,
+                eta=a_over_h * depth * np.cos(k * x), u=np.zeros(m), v=None, w=np.zeros(m), dt=T / steps,
+                steps=steps, g=G, rho=RHO, m=m, walls=True, relax=None, k=k, omega=float(om))
