@@ -6,7 +6,7 @@
  * sigma levels sigma_j = j/(nz-1), j = 0..nz-1, plus one ghost level j = -1
  * below the bed.  Node (ix, iy, j) has index ((j+1)*ny + iy)*nx + ix.
  *
- * Walls (2-D, Sec. 5.1 and the flume of Sec. 5.3): the impermeable walls at
+ * Walls (2-D; ghost nodes of Sec. 3, the flume of Sec. 5.2): the impermeable walls at
  * x = 0 and x = lx carry the Neumann condition n . grad p = n . G through one
  * ghost column outside each wall (columns 0 and nx-1).  The row of ghost node
  * (0, j) is the wall condition n . grad^(i-1) p = n . G evaluated at the wall

@@ -38,7 +38,7 @@ typedef struct {
     int nx, ny, nz;   /* columns in x and y (ny = 1 in 2D), sigma levels 0..nz-1 (ghost level -1 extra) */
     double lx, ly;    /* periodic lengths in x and y; with walls, lx is the wall-to-wall length */
     int walls;        /* 0: periodic in x.  1 (2-D only): vertical walls at x = 0 and x = lx, with
-                         columns 0 and nx-1 the ghost columns outside them (Sec. 5.1, Sec. 5.3):
+                         columns 0 and nx-1 the ghost columns outside them (Sec. 3, Sec. 5.2):
                          physical columns 1..nx-2 sit at x = (ix-1) lx/(nx-3) */
 } or_grid;
 
@@ -142,7 +142,7 @@ int or_stage(or_problem *P, const or_physics *ph, int stage,
              double *u, double *v, double *w, double *eta,
              double *Ku, double *Kv, double *Kw, double *Keta, double *p, or_stats *st);
 
-/* ---- wave generation and absorption zones (physics.c, Sec. 5.3) ---- */
+/* ---- wave generation and absorption zones (physics.c, Sec. 5.2) ---- */
 typedef struct {
     double gen_x0, gen_x1;   /* generation zone [gen_x0, gen_x1] (empty when gen_x1 <= gen_x0) */
     double abs_x0, abs_x1;   /* absorption zone [abs_x0, abs_x1] (empty when abs_x1 <= abs_x0) */

@@ -18,7 +18,7 @@
  * ghost columns too.  The ghost columns carry no flow: f_eta and f_u are zero
  * there, so their state never changes.
  *
- * Generation and absorption zones (Sec. 5.3): after each stage the surface
+ * Generation and absorption zones (Sec. 5.2): after each stage the surface
  * and the velocities inside a zone are blended towards a target,
  * phi <- Gamma phi + (1 - Gamma) phi_target, with the relaxation weight of
  * Engsig-Karup, Bingham & Lindberg (J. Comput. Phys. 228, 2009),
