@@ -30,6 +30,17 @@
  * ((j+1)*ny + iy)*nx + ix.  Surface fields (eta, h) hold nx*ny doubles,
  * index iy*nx + ix.  Requirements: nz >= 7; nx and ny (when ny > 1) are
  * multiples of 4 and at least 8.
+ *
+ * Walls (sw_grid.walls = 1; 2-D only, nx >= 16 and a multiple of 4): vertical walls at
+ * x = 0 and x = lx with impermeable (Neumann) conditions imposed through
+ * ghost nodes (Sec. 3; the flume of Sec. 5.2).  Columns 0 and nx-1 are ghost
+ * columns one spacing outside the walls; the physical columns 1..nx-2 sit at
+ * x = (ix-1) lx/(nx-3).  The row of ghost node (0, j), j = -1..nz-2, is the
+ * wall condition n . grad^(i-1) p = n . G at the wall node (1, j) (likewise
+ * nx-1 for the wall node nx-2); surface ghost nodes are Dirichlet rows.  x
+ * stencils next to a wall are shifted inside the grid (off-centred 7-point
+ * formulas); x derivatives of surface data and velocities use the physical
+ * columns only.  The stage driver keeps the ghost columns' flow at rest.
  */
 #ifndef SAWAVE_H
 #define SAWAVE_H
@@ -57,7 +68,9 @@ typedef struct sw_problem sw_problem;
 
 typedef struct {
     int nx, ny, nz;  /* columns in x and y, sigma levels (ghost level not counted) */
-    double lx, ly;   /* periodic domain lengths (ly ignored when ny == 1) */
+    double lx, ly;   /* periodic domain lengths (ly ignored when ny == 1); with walls, lx is the
+                        wall-to-wall length */
+    int walls;       /* 0: periodic in x; 1: walls with ghost columns (2-D, see above) */
 } sw_grid;
 
 typedef struct {
@@ -94,6 +107,24 @@ typedef struct {
     double rho;  /* density */
     double dt;   /* time step Delta tau */
 } sw_physics;
+
+/* Wave generation and absorption zones of a flume (Sec. 5.2).  After every
+ * stage, eta, u and w of the physical columns inside a zone are blended
+ * towards a target, phi <- Gamma phi + (1 - Gamma) phi_target, with
+ * Gamma(xi) = 1 - (exp(xi^3.5) - 1)/(e - 1) (Engsig-Karup, Bingham & Lindberg
+ * 2009), xi = 0 at the inner end of the zone and 1 at its outer end.  The
+ * generation target is the incident linear wave of height H and period T on
+ * the still-water depth `depth`, amplitude ramped in time by
+ * (1 - cos(pi t / ramp_time))/2 up to t = ramp_time; the absorption target is
+ * still water.  The zone x ranges are in the coordinates of the grid. */
+typedef struct {
+    double gen_x0, gen_x1;   /* generation zone (empty when gen_x1 <= gen_x0); xi = 1 at gen_x0 */
+    double abs_x0, abs_x1;   /* absorption zone (empty when abs_x1 <= abs_x0); xi = 1 at abs_x1 */
+    double height, period;   /* incident wave height H and period T */
+    double depth;            /* still-water depth of the incident wave */
+    double ramp_time;        /* 0 for no ramp */
+    double g;                /* gravity of the dispersion relation */
+} sw_relaxation;
 
 /* Build a problem on the current CUDA device.  h_depth: host array of nx*ny
  * still-water depths h > 0.  Computes the ILU(0) factors of the operator at
@@ -153,16 +184,22 @@ int sw_draw_omega(uint64_t seed, long long solve_index, int k, double *h_omega);
 /* Physical constants and time step for the stage driver. */
 int sw_set_physics(sw_problem *p, const sw_physics *phys);
 /* Load the state: u, w (and v in 3-D, else NULL) on the m nodes, eta on the
- * surface; the Runge-Kutta registers are zeroed and the stage counter reset.
- * Device pointers, copied. */
+ * surface; the Runge-Kutta registers are zeroed, the stage counter and the
+ * time (t = 0) reset.  Device pointers, copied. */
 int sw_set_state(sw_problem *p, const double *d_u, const double *d_v, const double *d_w,
                  const double *d_eta, void *stream);
 /* Copy the state out (any of the pointers may be NULL). */
 int sw_get_state(sw_problem *p, double *d_u, double *d_v, double *d_w, double *d_eta,
                  double *d_p, void *stream);
 /* One stage i (cycling 1..5) of Algorithm 1: K_eta and eta^(i), the right-hand
- * side of Eq. (16)-(17), the Poisson solve, K_u and u^(i). */
+ * side of Eq. (16)-(17), the Poisson solve, K_u and u^(i); then, when
+ * relaxation zones are set, the blend of eta, u, w at the stage's end time
+ * t = (n + c_(i+1)) dt (n completed steps, c_6 = 1). */
 int sw_advance_stage(sw_problem *p, void *stream);
+/* Generation/absorption zones applied after every stage (2-D); NULL removes
+ * them.  Copied.  SW_ERR_BAD_ARG for a 3-D problem or a non-positive period,
+ * height or depth when a generation zone is set. */
+int sw_set_relaxation(sw_problem *p, const sw_relaxation *relax);
 /* The system A(eta_prev, eta_cur) p = b of the last stage (copies; any pointer may be NULL). */
 int sw_get_last_system(sw_problem *p, double *d_eta_prev, double *d_eta_cur, double *d_b, void *stream);
 
@@ -182,7 +219,8 @@ int sw_destroy_batch(sw_batch *b);
  * problems were given to sw_create_batch.  Per-member results via sw_get_stats. */
 int sw_batch_solve(sw_batch *b, const double *const *d_eta_prev, const double *const *d_eta_cur,
                    const double *const *d_b, double *const *d_x, void *stream);
-/* One Runge-Kutta stage of every member (each needs its state and physics set). */
+/* One Runge-Kutta stage of every member (each needs its state and physics set).
+ * Relaxation zones set with sw_set_relaxation are not applied here. */
 int sw_batch_advance_stage(sw_batch *b, void *stream);
 
 /* Allocation-free operator apply: y = A(eta_prev, eta_cur) x as in
@@ -197,7 +235,7 @@ int sw_batch_advance_stage(sw_batch *b, void *stream);
  * larger grids return SW_ERR_BAD_ARG.  The first call on a device resolves
  * the array's address and should come before any stream capture.  Calls share
  * the array: two calls that overlap on the GPU race.  Same grid rules as
- * sw_create_problem. */
+ * sw_create_problem; periodic grids only (walls: SW_ERR_BAD_ARG). */
 int sw_apply_operator_noalloc(const sw_grid *grid, const double *d_h, const double *d_eta_prev,
                               const double *d_eta_cur, const double *d_x, double *d_y, void *stream);
 

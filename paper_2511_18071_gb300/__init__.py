@@ -14,7 +14,7 @@ from . import build as _build
 __all__ = ["Grid", "Params", "Stats", "Physics", "Problem", "create_problem", "destroy_problem", "problem_size",
            "solve_poisson", "solve_poisson_host", "get_stats", "apply_operator", "apply_preconditioner",
            "subspace_guess", "apply_operator_noalloc", "get_sketch", "set_sketch", "draw_omega", "set_physics", "set_state", "get_state",
-           "advance_stage", "create_batch", "destroy_batch", "batch_solve", "batch_advance_stage", "Batch",
+           "advance_stage", "set_relaxation", "Relaxation", "create_batch", "destroy_batch", "batch_solve", "batch_advance_stage", "Batch",
            "get_last_system", "get_phase_times", "enable_timing", "get_solve_time", "library_path", "SawaveError", "GUESS",
            "PRECISION"]
 
@@ -31,7 +31,14 @@ class SawaveError(RuntimeError):
 
 
 class Grid(C.Structure):
-    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double), ("ly", C.c_double)]
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double), ("ly", C.c_double),
+                ("walls", C.c_int)]
+
+
+class Relaxation(C.Structure):
+    _fields_ = [("gen_x0", C.c_double), ("gen_x1", C.c_double), ("abs_x0", C.c_double), ("abs_x1", C.c_double),
+                ("height", C.c_double), ("period", C.c_double), ("depth", C.c_double), ("ramp_time", C.c_double),
+                ("g", C.c_double)]
 
 
 class Params(C.Structure):
@@ -87,6 +94,7 @@ def lib():
         L.sw_set_state.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sw_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.sw_advance_stage.argtypes = [vp, vp]
+        L.sw_set_relaxation.argtypes = [vp, C.POINTER(Relaxation)]
         L.sw_enable_timing.argtypes = [vp, ip]
         L.sw_get_last_system.argtypes = [vp, vp, vp, vp, vp]
         L.sw_apply_operator_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp, vp, vp, vp]
@@ -102,7 +110,7 @@ def lib():
                      "sw_subspace_guess", "sw_get_sketch", "sw_set_sketch", "sw_draw_omega", "sw_set_physics",
                      "sw_set_state", "sw_get_state", "sw_advance_stage", "sw_enable_timing", "sw_get_solve_time",
                      "sw_get_last_system", "sw_apply_operator_noalloc", "sw_get_phase_times", "sw_create_batch",
-                     "sw_destroy_batch", "sw_batch_solve", "sw_batch_advance_stage"]:
+                     "sw_destroy_batch", "sw_batch_solve", "sw_batch_advance_stage", "sw_set_relaxation"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -232,6 +240,14 @@ def advance_stage(p, stream=None):
     return _check(lib().sw_advance_stage(p, _stream(stream)))
 
 
+def set_relaxation(p, relax):
+    """Generation/absorption zones after every stage (an sw_relaxation, a dict of its fields, or None)."""
+    if relax is None:
+        return _check(lib().sw_set_relaxation(p, None))
+    rl = relax if isinstance(relax, Relaxation) else Relaxation(**relax)
+    return _check(lib().sw_set_relaxation(p, C.byref(rl)))
+
+
 def get_last_system(p, eta_prev=None, eta_cur=None, b=None, stream=None):
     return _check(lib().sw_get_last_system(p, _dptr(eta_prev), _dptr(eta_cur), _dptr(b), _stream(stream)))
 
@@ -314,8 +330,8 @@ class Problem:
     """Owning handle around sw_problem with torch-tensor conveniences."""
 
     def __init__(self, nx, ny, nz, lx, ly, h, restart=20, max_restarts=50, tol=1e-8, guess="cold", k=10,
-                 decay=0.9, n_init_solves=30, precision="fp64", seed=2511):
-        self.grid = Grid(nx, ny, nz, lx, ly if ny > 1 else 0.0)
+                 decay=0.9, n_init_solves=30, precision="fp64", seed=2511, walls=False):
+        self.grid = Grid(nx, ny, nz, lx, ly if ny > 1 else 0.0, int(bool(walls)))
         self.params = Params(restart, max_restarts, tol, GUESS[guess], k, decay, n_init_solves,
                              PRECISION[precision], seed)
         self.handle = create_problem(self.grid, self.params, h)

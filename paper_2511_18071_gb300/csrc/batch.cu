@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_solve_kernel(const BatchIte
         const Dev D = items[i].D;
         const SolveArgs A = items[i].A;
         BlockTeam tm;
-        solve_body<BlockTeam, TI>(tm, D, A, S, smem_raw + BSMEM_FIXED, nullptr);
+        solve_body<BlockTeam, TI, 2>(tm, D, A, S, smem_raw + BSMEM_FIXED, nullptr);
         __syncthreads();
     }
 }

@@ -10,6 +10,7 @@
 //     interior rows grad^(i) . G, ghost rows n . G at the bed, surface rows 0;
 //   the Poisson solve A(eta^(i-1), eta^(i)) p = b (Algorithm 2);
 //   f_u (Eq. 14a) with grad^(i-1), K_u <- alpha_i K_u + dt f_u, u^(i) = u + beta_i K_u.
+#include <cmath>
 #include <cstring>
 #include <utility>
 
@@ -41,6 +42,26 @@ __global__ void fu_kernel(Dev D, DrvPtrs q) {
 __global__ void update_kernel(Dev D, DrvPtrs q) {
     long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (node < D.m) update_at(D, q, node);
+}
+__global__ void relax_kernel(Dev D, DrvPtrs q, RelaxArgs ra) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < D.ncol) relax_column(D, q, ra, c);
+}
+
+// Wavenumber of the linear dispersion relation omega^2 = g k tanh(k h) by
+// Newton's method from the deep-water value (the residual is increasing and
+// concave in k, so the iteration converges monotonically).
+static double dispersion_k(double omega, double depth, double g) {
+    double k = omega * omega / g;
+    for (int it = 0; it < 100; ++it) {
+        const double th = std::tanh(k * depth);
+        const double F = g * k * th - omega * omega;
+        const double dF = g * th + g * k * depth * (1.0 - th * th);
+        const double dk = F / dF;
+        k -= dk;
+        if (std::fabs(dk) <= 1e-15 * k) break;
+    }
+    return k;
 }
 
 DrvPtrs driver_ptrs(Problem *P) {
@@ -102,6 +123,7 @@ extern "C" int sw_set_state(sw_problem *pp, const double *u, const double *v, co
     if (e == cudaSuccess) e = cudaMemsetAsync(P->d_Keta, 0, nb, s);
     if (e != cudaSuccess) return cuda_fail(e, "set state");
     P->stage = 0;
+    P->step_index = 0;
     P->has_state = true;
     P->last_stream = s;
     return SW_OK;
@@ -149,6 +171,23 @@ extern "C" int sw_advance_stage(sw_problem *pp, void *stream) {
     // eta^(i) becomes the state; the buffer of eta^(i-1) is kept for sw_get_last_system
     std::swap(P->d_eta, P->d_eta_new);
     P->launches += 6;
+    if (P->relax_on) {
+        // generation/absorption zones at the stage's end time t_n + c_(i+1) dt (t_n + dt after stage 5)
+        const double c_next = P->stage < 4 ? LS_C[P->stage + 1] : 1.0;
+        const double t = ((double)P->step_index + c_next) * P->phys.dt;
+        const sw_relaxation &rl = P->relax;
+        const double pi = 3.14159265358979323846;
+        double ramp = 1.0;
+        if (rl.ramp_time > 0.0 && t < rl.ramp_time) ramp = 0.5 * (1.0 - std::cos(pi * t / rl.ramp_time));
+        RelaxArgs ra{rl.gen_x0, rl.gen_x1, rl.abs_x0, rl.abs_x1, 0.5 * rl.height * ramp, P->relax_k,
+                     2.0 * pi / rl.period, rl.depth, t};
+        DrvPtrs q2 = driver_ptrs(P);   // q2.eta is eta^(i) after the swap
+        relax_kernel<<<gc, T, 0, s>>>(D, q2, ra);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "relaxation launch");
+        P->launches += 1;
+    }
+    if (P->stage == 4) P->step_index++;
     P->stage = (P->stage + 1) % 5;
     P->last_stream = s;
     return SW_OK;
@@ -164,5 +203,21 @@ extern "C" int sw_get_last_system(sw_problem *pp, double *ep, double *ec, double
     if (e == cudaSuccess && ec) e = cudaMemcpyAsync(ec, P->d_eta, nb, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && b) e = cudaMemcpyAsync(b, P->d_rhs, P->m * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "get last system");
+    return SW_OK;
+}
+
+extern "C" int sw_set_relaxation(sw_problem *pp, const sw_relaxation *rl) {
+    Problem *P = (Problem *)pp;
+    if (!P) { set_error("null problem"); return SW_ERR_BAD_ARG; }
+    if (!rl) { P->relax_on = false; return SW_OK; }
+    if (P->dev.three_d) { set_error("relaxation zones: 2-D problems only"); return SW_ERR_BAD_ARG; }
+    const bool gen = rl->gen_x1 > rl->gen_x0;
+    if (gen && (!(rl->period > 0) || !(rl->height >= 0) || !(rl->depth > 0) || !(rl->g > 0))) {
+        set_error("relaxation zones: generation needs period > 0, height >= 0, depth > 0, g > 0");
+        return SW_ERR_BAD_ARG;
+    }
+    P->relax = *rl;
+    P->relax_k = gen ? dispersion_k(2.0 * 3.14159265358979323846 / rl->period, rl->depth, rl->g) : 0.0;
+    P->relax_on = true;
     return SW_OK;
 }

@@ -167,6 +167,10 @@ extern "C" int sw_apply_operator_noalloc(const sw_grid *grid, const double *d_h,
         set_error("grid: need nx (and ny in 3-D) multiples of 4 and >= 8, 7 <= nz <= 63, positive lengths");
         return SW_ERR_BAD_ARG;
     }
+    if (g.walls) {
+        set_error("sw_apply_operator_noalloc: periodic grids only");
+        return SW_ERR_BAD_ARG;
+    }
     if ((long long)g.nx * g.ny > SW_NOALLOC_MAX_COLUMNS) {
         set_error("sw_apply_operator_noalloc: nx*ny exceeds the static scratch limit of 65536 columns");
         return SW_ERR_BAD_ARG;

@@ -1,14 +1,16 @@
 // Host-side set-up of a problem: finite-difference weights, the still-water
-// operator in slot form, its ILU(0) factorisation in the four-colour column
+// operator in slot form, its ILU(0) factorisation in the column-group
 // ordering, and the device allocations.
 //
 // Preconditioner (Sec. 3 and Sec. 5): one incomplete LU factorisation of the
 // operator built for the still-water state eta = 0, computed once and reused
 // for every stage.  Variant ILU(0): fill restricted to the sparsity pattern of
-// that operator.  Ordering: colour (ix + iy) mod 4 first, then the column, then
-// the level from the ghost level up; with nx, ny multiples of four, columns of
-// one colour never share a 7-point stencil, which lets the device sweep all
-// columns of a colour at once.
+// that operator.  Ordering: column group first, then the column, then the level
+// from the ghost level up.  Periodic grids use the colours (ix + iy) mod 4:
+// with nx, ny multiples of four, columns of one colour never share a 7-point
+// stencil, which lets the device sweep all columns of a colour at once.  With
+// walls, the six columns next to the walls (whose rows reach 7 columns
+// inwards) form three more groups after the four colours.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -58,44 +60,85 @@ static int sigma_window(int nz, int j) {
 namespace {
 
 struct Host {
-    int nx, ny, nz, P, ncol, layout, nslot, three_d;
+    int nx, ny, nz, P, ncol, layout, nslot, three_d, walls;
     long long m;
     double dx, dy;
     double wx1[W], wx2[W], wy1[W], wy2[W];
+    double wxo1[W][W], wxo2[W][W];  // walls: weights at node o of a window of 7 equispaced nodes
     std::vector<double> ws1, ws2;   // P x W
     std::vector<int> win;           // P
     std::vector<double> h, hx, hy, hxx, hyy;
+    // column groups of the factorisation order (see build_groups)
+    int ngroups = 4;
+    std::vector<int> goff, gcol, colrank;
+    std::vector<unsigned char> grp;
 
-    int colour(int ix, int iy) const { return (ix + iy) & 3; }
-    long long rank_of(int ix, int iy, int j) const {
-        int c = colour(ix, iy);
-        long long q = (long long)iy * (nx / 4) + (ix >> 2);
-        return ((long long)c * (ncol / 4) + q) * P + (j + 1);
+    // Periodic: colour (ix + iy) mod 4, columns in index order within a colour.
+    // Walls: the rows of columns 0-2 and nx-3..nx-1 reach 7 columns inwards, so
+    // those six columns form three groups {0, nx-1}, {1, nx-2}, {2, nx-3} after
+    // the four colours ix mod 4 of columns 3..nx-4.  No two columns of one group
+    // share a row's x window.
+    void build_groups() {
+        gcol.clear();
+        ngroups = walls ? 7 : 4;
+        goff.assign(ngroups + 1, 0);
+        grp.assign(ncol, 0);
+        for (int c = 0; c < 4; ++c) {
+            goff[c] = (int)gcol.size();
+            if (walls) {
+                for (int ix = 3; ix <= nx - 4; ++ix)
+                    if (ix % 4 == c) gcol.push_back(ix);
+            } else {
+                for (int iy = 0; iy < ny; ++iy)
+                    for (int ix = 0; ix < nx; ++ix)
+                        if (((ix + iy) & 3) == c) gcol.push_back(iy * nx + ix);
+            }
+        }
+        if (walls)
+            for (int e = 0; e < 3; ++e) {
+                goff[4 + e] = (int)gcol.size();
+                gcol.push_back(e);
+                gcol.push_back(nx - 1 - e);
+            }
+        goff[ngroups] = (int)gcol.size();
+        colrank.assign(ncol, 0);
+        for (int g = 0; g < ngroups; ++g)
+            for (int r = goff[g]; r < goff[g + 1]; ++r) {
+                colrank[gcol[r]] = r;
+                grp[gcol[r]] = (unsigned char)g;
+            }
     }
+    long long rank_of(int ix, int iy, int j) const { return (long long)colrank[iy * nx + ix] * P + (j + 1); }
     void node_of_rank(long long r, int &ix, int &iy, int &j) const {
-        long long per = (long long)(ncol / 4) * P;
-        int c = (int)(r / per);
-        long long rem = r % per;
-        long long q = rem / P;
-        j = (int)(rem % P) - 1;
-        iy = (int)(q / (nx / 4));
-        ix = ((c - iy) & 3) + 4 * (int)(q % (nx / 4));
+        const int col = gcol[r / P];
+        j = (int)(r % P) - 1;
+        ix = col % nx;
+        iy = col / nx;
     }
     int wrapx(int i) const { i %= nx; return i < 0 ? i + nx : i; }
     int wrapy(int i) const { i %= ny; return i < 0 ? i + ny : i; }
+    // x window of the unknowns at column ix: first column (walls) and position of ix in it
+    int xs(int ix) const { return walls ? std::min(std::max(ix - HALF, 0), nx - W) : ix - HALF; }
+    int own_pos(int ix) const { return ix - xs(ix); }
+    int xcol(int ix, int t) const { return walls ? xs(ix) + t : wrapx(ix - HALF + t); }
+    const double *xw1(int ix) const { return walls ? wxo1[own_pos(ix)] : wx1; }
+    const double *xw2(int ix) const { return walls ? wxo2[own_pos(ix)] : wx2; }
+    bool ghost_col(int ix) const { return walls && (ix == 0 || ix == nx - 1); }
 
     // neighbour of slot s for row (ix, iy, j)
     void slot_nb(int s, int ix, int iy, int j, int &nx_, int &ny_, int &lev) const {
         static const int off[6] = {-3, -2, -1, 1, 2, 3};
         int ox = 0, oy = 0;
         int w0 = win[j + 1];
+        const int o = own_pos(ix);
         switch (layout) {
         case CROSS2D:
-            if (s < 6) { ox = off[s]; lev = j; } else { lev = w0 + (s - 6); }
-            break;
+            if (s < 6) { nx_ = xcol(ix, s < o ? s : s + 1); lev = j; } else { nx_ = ix; lev = w0 + (s - 6); }
+            ny_ = 0;
+            return;
         case BOX2D:
-            ox = s / 7 - 3; lev = w0 + s % 7;
-            break;
+            nx_ = xcol(ix, s / 7); lev = w0 + s % 7; ny_ = 0;
+            return;
         case CROSS3D:
             if (s < 6) { ox = off[s]; lev = j; }
             else if (s < 12) { oy = off[s - 6]; lev = j; }
@@ -108,11 +151,19 @@ struct Host {
         nx_ = wrapx(ix + ox);
         ny_ = ny > 1 ? wrapy(iy + oy) : 0;
     }
-    // structural pattern of the still-water operator in this row
-    bool in_pattern(int s, int j) const {
-        if (j == nz - 1) return s == sigma_slot(layout, W - 1);
+    // structural pattern of the still-water operator in row (ix, j)
+    bool in_pattern(int s, int ix, int j) const {
+        const int o = three_d ? HALF : own_pos(ix);
+        if (j == nz - 1) return s == own_slot(layout, W - 1, o);
+        if (ghost_col(ix)) {
+            // wall row: x window at the row's level, and (box) the wall column's sigma window
+            const int kkj = j - win[j + 1];
+            if (layout == CROSS2D) return s < 6 || s == 6 + kkj;
+            const int tw = (ix == 0 ? 1 : nx - 2) - xs(ix);
+            return s % 7 == kkj || s / 7 == tw;
+        }
         if (j == -1) {
-            int ss = sigma_slot(layout, 0);
+            int ss = own_slot(layout, 0, o);
             if (s >= ss && s < ss + W) return true;
             if (layout == CROSS2D || layout == CROSS3D) return false;
             // box: horizontal entries at the bed level (window offset 1)
@@ -123,20 +174,32 @@ struct Host {
     }
     // slot of row (ix, iy, j) that refers to node (bx, by, lev), or -1
     int find_slot(int ix, int iy, int j, int bx, int by, int lev) const {
+        int kk = lev - win[j + 1];
+        auto xoff = [](int o) { return o < 0 ? o + 3 : o + 2; };  // -3..-1,1..3 -> 0..5
+        if (!three_d) {
+            int t;
+            if (walls) {
+                t = bx - xs(ix);
+            } else {
+                int dxo = bx - ix;
+                if (dxo > nx / 2) dxo -= nx;
+                if (dxo < -nx / 2) dxo += nx;
+                t = dxo + HALF;
+            }
+            const int o = own_pos(ix);
+            if (t < 0 || t >= W) return -1;
+            if (layout == CROSS2D) {
+                if (t == o) return (kk >= 0 && kk < W) ? 6 + kk : -1;
+                return lev == j ? (t < o ? t : t - 1) : -1;
+            }
+            return (kk >= 0 && kk < W) ? t * 7 + kk : -1;
+        }
         int dxo = bx - ix, dyo = by - iy;
         if (dxo > nx / 2) dxo -= nx;
         if (dxo < -nx / 2) dxo += nx;
-        if (ny > 1) { if (dyo > ny / 2) dyo -= ny; if (dyo < -ny / 2) dyo += ny; }
-        int kk = lev - win[j + 1];
-        auto xoff = [](int o) { return o < 0 ? o + 3 : o + 2; };  // -3..-1,1..3 -> 0..5
+        if (dyo > ny / 2) dyo -= ny;
+        if (dyo < -ny / 2) dyo += ny;
         switch (layout) {
-        case CROSS2D:
-            if (dxo == 0) return (kk >= 0 && kk < W) ? 6 + kk : -1;
-            if (lev == j && dxo >= -3 && dxo <= 3) return xoff(dxo);
-            return -1;
-        case BOX2D:
-            if (dxo >= -3 && dxo <= 3 && kk >= 0 && kk < W) return (dxo + 3) * 7 + kk;
-            return -1;
         case CROSS3D:
             if (dxo == 0 && dyo == 0) return (kk >= 0 && kk < W) ? 12 + kk : -1;
             if (lev != j) return -1;
@@ -152,31 +215,48 @@ struct Host {
     }
 
     // Row of the still-water operator (eta = 0, d = h) in slot form,
-    // following Eq. (16)-(18) with the push-forward of Eq. (9b) and (13b-13d).
+    // following Eq. (16)-(18) with the push-forward of Eq. (9b) and (13b-13d);
+    // with walls, the ghost-column rows are the wall conditions of Sec. 3.
     void a0_row(int ix, int iy, int j, double *v) const {
         for (int s = 0; s < nslot; ++s) v[s] = 0.0;
         int c = iy * nx + ix;
-        if (j == nz - 1) { v[sigma_slot(layout, W - 1)] = 1.0; return; }
+        const int o = three_d ? HALF : own_pos(ix);
+        if (j == nz - 1) { v[own_slot(layout, W - 1, o)] = 1.0; return; }
+        bool box = layout == BOX2D || layout == BOX3D;
+        if (ghost_col(ix)) {
+            // n . grad p at the wall node (iw, j), n = (-1, 0) at x = 0 and (1, 0) at x = lx
+            const int iw = ix == 0 ? 1 : nx - 2;
+            const double nxs = ix == 0 ? -1.0 : 1.0;
+            const double *w1x = xw1(iw);
+            for (int t = 0; t < W; ++t) v[find_slot(ix, iy, j, xcol(iw, t), 0, j)] += nxs * w1x[t];
+            if (box) {
+                const double sg = (double)j / (nz - 1);
+                const double a = (hx[iw] - sg * hx[iw]) / h[iw];   // sigma_x at still water
+                for (int kk = 0; kk < W; ++kk)
+                    v[find_slot(ix, iy, j, iw, 0, win[j + 1] + kk)] += nxs * a * ws1[(j + 1) * W + kk];
+            }
+            return;
+        }
         double d = h[c], f = 1.0 / d;
         double gx = hx[c], gy = three_d ? hy[c] : 0.0;
-        bool box = layout == BOX2D || layout == BOX3D;
+        const double *w1x = xw1(ix), *w2x = xw2(ix);
         if (j == -1) {
             double nrm = 1.0 / std::sqrt(1.0 + gx * gx + gy * gy);
             double a0 = gx * f, a0y = gy * f;
             double cs = -nrm * (gx * a0 + gy * a0y + f);
             const double *w1 = &ws1[1 * W];   // sigma weights of level 0
-            for (int kk = 0; kk < W; ++kk) v[sigma_slot(layout, kk)] += cs * w1[kk];
+            for (int kk = 0; kk < W; ++kk) v[own_slot(layout, kk, o)] += cs * w1[kk];
             if (box) {
-                for (int t = -HALF; t <= HALF; ++t) {
-                    if (t == 0) {
-                        v[sigma_slot(layout, 1)] += -nrm * gx * wx1[t + HALF] - nrm * gy * (three_d ? wy1[t + HALF] : 0.0);
+                for (int t = 0; t < W; ++t) {
+                    if (t == o) {
+                        v[own_slot(layout, 1, o)] += -nrm * gx * w1x[t] - nrm * gy * (three_d ? wy1[t] : 0.0);
                         continue;
                     }
-                    int s = find_slot(ix, iy, j, wrapx(ix + t), iy, 0);
-                    v[s] += -nrm * gx * wx1[t + HALF];
+                    int s = find_slot(ix, iy, j, xcol(ix, t), iy, 0);
+                    v[s] += -nrm * gx * w1x[t];
                     if (three_d) {
-                        int s2 = find_slot(ix, iy, j, ix, wrapy(iy + t), 0);
-                        v[s2] += -nrm * gy * wy1[t + HALF];
+                        int s2 = find_slot(ix, iy, j, ix, wrapy(iy + t - HALF), 0);
+                        v[s2] += -nrm * gy * wy1[t];
                     }
                 }
             }
@@ -197,23 +277,23 @@ struct Host {
         }
         double c_ss = a * a + ay * ay + f * f;
         double c_s = ax + a * as + ayy + ay * ays;
-        for (int t = -HALF; t <= HALF; ++t) {
-            int s = find_slot(ix, iy, j, wrapx(ix + t), iy, j);
-            v[s] += wx2[t + HALF];
+        for (int t = 0; t < W; ++t) {
+            int s = find_slot(ix, iy, j, xcol(ix, t), iy, j);
+            v[s] += w2x[t];
             if (three_d) {
-                int s2 = find_slot(ix, iy, j, ix, wrapy(iy + t), j);
-                v[s2] += wy2[t + HALF];
+                int s2 = find_slot(ix, iy, j, ix, wrapy(iy + t - HALF), j);
+                v[s2] += wy2[t];
             }
         }
-        for (int kk = 0; kk < W; ++kk) v[sigma_slot(layout, kk)] += c_ss * w2[kk] + c_s * w1[kk];
+        for (int kk = 0; kk < W; ++kk) v[own_slot(layout, kk, o)] += c_ss * w2[kk] + c_s * w1[kk];
         if (box) {
-            for (int t = -HALF; t <= HALF; ++t)
+            for (int t = 0; t < W; ++t)
                 for (int kk = 0; kk < W; ++kk) {
-                    int s = find_slot(ix, iy, j, wrapx(ix + t), iy, w0 + kk);
-                    v[s] += 2.0 * a * wx1[t + HALF] * w1[kk];
+                    int s = find_slot(ix, iy, j, xcol(ix, t), iy, w0 + kk);
+                    v[s] += 2.0 * a * w1x[t] * w1[kk];
                     if (three_d) {
-                        int s2 = find_slot(ix, iy, j, ix, wrapy(iy + t), w0 + kk);
-                        v[s2] += 2.0 * ay * wy1[t + HALF] * w1[kk];
+                        int s2 = find_slot(ix, iy, j, ix, wrapy(iy + t - HALF), w0 + kk);
+                        v[s2] += 2.0 * ay * wy1[t] * w1[kk];
                     }
                 }
         }
@@ -223,19 +303,19 @@ struct Host {
 // ILU(0), row by row in rank order (IKJ form): for each row i and each entry
 // k < i of its pattern in increasing order, l_ik = a_ik / u_kk, then
 // a_ij -= l_ik u_kj for every j > k present in both row k and row i.
-// Rows of one column are consecutive ranks and only reference lower colours
-// or the same column, so the columns of one colour are factorised in parallel.
+// Rows of one column are consecutive ranks and only reference earlier groups
+// or the same column, so the columns of one group are factorised in parallel.
 static void factorise_column(const Host &H, int c, int q, std::vector<double> &lu, std::vector<double> &udinv,
                              std::vector<double> &v, std::vector<std::pair<long long, int>> &lower, int &status) {
     const int ns = H.nslot;
     for (int a = 0; a < H.P; ++a) {
-        const long long i = ((long long)c * (H.ncol / 4) + q) * H.P + a;
+        const long long i = ((long long)H.goff[c] + q) * H.P + a;
         int ix, iy, j;
         H.node_of_rank(i, ix, iy, j);
         H.a0_row(ix, iy, j, v.data());
         lower.clear();
         for (int s = 0; s < ns; ++s) {
-            if (!H.in_pattern(s, j)) { v[s] = 0.0; continue; }
+            if (!H.in_pattern(s, ix, j)) { v[s] = 0.0; continue; }
             int bx, by, bl;
             H.slot_nb(s, ix, iy, j, bx, by, bl);
             long long k = H.rank_of(bx, by, bl);
@@ -251,16 +331,16 @@ static void factorise_column(const Host &H, int c, int q, std::vector<double> &l
             H.node_of_rank(k, kx, ky, kj);
             const double *rowk = &lu[(size_t)k * ns];
             for (int s2 = 0; s2 < ns; ++s2) {
-                if (!H.in_pattern(s2, kj)) continue;
+                if (!H.in_pattern(s2, kx, kj)) continue;
                 int bx, by, bl;
                 H.slot_nb(s2, kx, ky, kj, bx, by, bl);
                 if (H.rank_of(bx, by, bl) <= k) continue;
                 int s3 = H.find_slot(ix, iy, j, bx, by, bl);
-                if (s3 < 0 || !H.in_pattern(s3, j)) continue;
+                if (s3 < 0 || !H.in_pattern(s3, ix, j)) continue;
                 v[s3] -= l * rowk[s2];
             }
         }
-        const double ud = v[sigma_slot(H.layout, j - H.win[j + 1])];
+        const double ud = v[own_slot(H.layout, j - H.win[j + 1], H.three_d ? HALF : H.own_pos(ix))];
         if (ud == 0.0 || !std::isfinite(ud)) { status = SW_ERR_SINGULAR_PRECOND; return; }
         udinv[i] = 1.0 / ud;
         std::copy(v.begin(), v.end(), lu.begin() + (size_t)i * ns);
@@ -272,12 +352,12 @@ static int factorise(const Host &H, std::vector<double> &lu, std::vector<double>
     const long long m = H.m;
     lu.assign((size_t)m * ns, 0.0);   // row-major during the factorisation
     udinv.assign((size_t)m, 0.0);
-    const int per = H.ncol / 4;
     unsigned hw = std::thread::hardware_concurrency();
     int nt = (int)std::max(1u, std::min(hw ? hw : 1u, 32u));
     if (m < 20000) nt = 1;
     std::vector<int> status(nt, SW_OK);
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < H.ngroups; ++c) {
+        const int per = H.goff[c + 1] - H.goff[c];
         auto work = [&](int t) {
             std::vector<double> v(ns);
             std::vector<std::pair<long long, int>> lower;
@@ -327,6 +407,10 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
         set_error("grid: need nx (and ny in 3-D) multiples of 4 and >= 8, 7 <= nz <= 63, positive lengths");
         return SW_ERR_BAD_ARG;
     }
+    if (g.walls != 0 && (g.walls != 1 || three_d || g.nx < 16)) {
+        set_error("grid: walls need a 2-D grid with nx >= 16");
+        return SW_ERR_BAD_ARG;
+    }
     if (p.restart < 1 || p.restart > MAX_RESTART || p.max_restarts < 0 || !(p.tol > 0) || p.guess < 0 ||
         p.guess > 2 || p.k < 1 || p.k > MAX_K || !(p.decay > 0) || p.decay > 1 || p.n_init_solves < 0 ||
         (p.precision != SW_PRECISION_FP64 && p.precision != SW_PRECISION_MIXED)) {
@@ -336,8 +420,9 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     Host H;
     H.nx = g.nx; H.ny = g.ny; H.nz = g.nz; H.P = g.nz + 1; H.ncol = g.nx * g.ny;
     H.three_d = three_d;
+    H.walls = g.walls;
     H.m = (long long)H.ncol * H.P;
-    H.dx = g.lx / g.nx;
+    H.dx = H.walls ? g.lx / (g.nx - 3) : g.lx / g.nx;
     H.dy = three_d ? g.ly / g.ny : 1.0;
     bool flat = true;
     H.h.assign(h_depth, h_depth + H.ncol);
@@ -351,6 +436,9 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
         long double xs[W];
         for (int t = 0; t < W; ++t) xs[t] = (long double)(t - HALF) * (long double)H.dx;
         lagrange_weights(xs, 0.0L, H.wx1, H.wx2);
+        // walls: every evaluation point o of a window of 7 equispaced nodes
+        for (int t = 0; t < W; ++t) xs[t] = (long double)t * (long double)H.dx;
+        for (int o = 0; o < W; ++o) lagrange_weights(xs, (long double)o * (long double)H.dx, H.wxo1[o], H.wxo2[o]);
         for (int t = 0; t < W; ++t) xs[t] = (long double)(t - HALF) * (long double)H.dy;
         lagrange_weights(xs, 0.0L, H.wy1, H.wy2);
         H.ws1.resize(H.P * W); H.ws2.resize(H.P * W); H.win.resize(H.P);
@@ -361,15 +449,24 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
             lagrange_weights(xs, (long double)j / (long double)(g.nz - 1), &H.ws1[(j + 1) * W], &H.ws2[(j + 1) * W]);
         }
     }
-    // surface-grid derivatives of the bathymetry (D_chi, D_gamma of Sec. 3)
+    // surface-grid derivatives of the bathymetry (D_chi, D_gamma of Sec. 3);
+    // with walls over the physical columns, a ghost column taking its wall column's
     H.hx.assign(H.ncol, 0.0); H.hy.assign(H.ncol, 0.0); H.hxx.assign(H.ncol, 0.0); H.hyy.assign(H.ncol, 0.0);
     for (int iy = 0; iy < g.ny; ++iy)
         for (int ix = 0; ix < g.nx; ++ix) {
             double s1 = 0, s2 = 0, t1 = 0, t2 = 0;
+            int xe = ix, x0 = ix - HALF;
+            const double *w1 = H.wx1, *w2 = H.wx2;
+            if (H.walls) {
+                xe = std::min(std::max(ix, 1), g.nx - 2);
+                x0 = std::min(std::max(xe - HALF, 1), g.nx - 1 - W);
+                w1 = H.wxo1[xe - x0];
+                w2 = H.wxo2[xe - x0];
+            }
             for (int t = -HALF; t <= HALF; ++t) {
-                double vx = H.h[iy * g.nx + H.wrapx(ix + t)];
-                s1 += H.wx1[t + HALF] * vx;
-                s2 += H.wx2[t + HALF] * vx;
+                double vx = H.h[iy * g.nx + H.wrapx(x0 + HALF + t)];
+                s1 += w1[t + HALF] * vx;
+                s2 += w2[t + HALF] * vx;
                 if (three_d) {
                     double vy = H.h[H.wrapy(iy + t) * g.nx + ix];
                     t1 += H.wy1[t + HALF] * vy;
@@ -379,6 +476,7 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
             int c = iy * g.nx + ix;
             H.hx[c] = s1; H.hxx[c] = s2; H.hy[c] = t1; H.hyy[c] = t2;
         }
+    H.build_groups();
     std::vector<double> lu_rows, udinv;
     int st = factorise(H, lu_rows, udinv);
     if (st != SW_OK) { set_error("zero pivot in ILU(0)"); return st; }
@@ -392,6 +490,8 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
         for (long long cr = 0; cr < H.ncol; ++cr) {
             std::fill(Lb.begin(), Lb.end(), 0.0);
             std::fill(Ub.begin(), Ub.end(), 0.0);
+            const int col = H.gcol[cr];
+            const int cix = col % H.nx, o = H.three_d ? HALF : H.own_pos(cix);
             for (int a = 0; a < Pl; ++a) {
                 int j = a - 1;
                 long long r = cr * Pl + a;
@@ -399,8 +499,9 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
                 Lb[a * Pl + a] = 1.0;
                 for (int kk = 0; kk < W; ++kk) {
                     int lev = w0 + kk, b = lev + 1;
-                    double v = lu_rows[(size_t)r * ns + sigma_slot(H.layout, kk)];
-                    if (!H.in_pattern(sigma_slot(H.layout, kk), j)) continue;
+                    const int so = own_slot(H.layout, kk, o);
+                    double v = lu_rows[(size_t)r * ns + so];
+                    if (!H.in_pattern(so, cix, j)) continue;
                     if (b < a) Lb[a * Pl + b] = v;
                     else Ub[a * Pl + b] = v;
                 }
@@ -442,8 +543,14 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     const int ns = H.nslot;
     int rc = SW_OK;
 #define ALLOC(ptr, bytes) do { if ((rc = dalloc(P, (void **)&(ptr), (bytes))) != SW_OK) { sw_destroy_problem((sw_problem *)P); return rc; } } while (0)
-    // weights: wx1, wx2, wy1, wy2, ws1 (P*7), ws2 (P*7)
-    std::vector<double> wts(4 * W + 2 * H.P * W);
+    // weights: wx1, wx2, wy1, wy2, ws1 (P*7), ws2 (P*7), wxo1 (7*7), wxo2 (7*7)
+    const size_t wxo_at = 4 * W + 2 * (size_t)H.P * W;
+    std::vector<double> wts(wxo_at + 2 * W * W);
+    for (int o = 0; o < W; ++o)
+        for (int t = 0; t < W; ++t) {
+            wts[wxo_at + o * W + t] = H.wxo1[o][t];
+            wts[wxo_at + W * W + o * W + t] = H.wxo2[o][t];
+        }
     std::copy(H.wx1, H.wx1 + W, wts.begin());
     std::copy(H.wx2, H.wx2 + W, wts.begin() + W);
     std::copy(H.wy1, H.wy1 + W, wts.begin() + 2 * W);
@@ -474,7 +581,13 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     ALLOC(P->d_omega, MAX_K * sizeof(double));
     ALLOC(P->d_stats, sizeof(DevStats));
     ALLOC(P->d_host_io, (3 * (size_t)m + 2 * (size_t)H.ncol) * sizeof(double));
+    ALLOC(P->d_gcol, (size_t)H.ncol * sizeof(int));
+    ALLOC(P->d_grp, (size_t)H.ncol);
+    ALLOC(P->d_goff, (MAX_GROUPS + 1) * sizeof(int));
     e = cudaMemcpy(P->d_weights, wts.data(), wts.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_gcol, H.gcol.data(), H.ncol * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_grp, H.grp.data(), H.ncol, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_goff, H.goff.data(), H.goff.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->d_win, H.win.data(), H.P * sizeof(int), cudaMemcpyHostToDevice);
     {
         std::vector<float> w32(wts.begin(), wts.end());
@@ -488,15 +601,16 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     std::copy(H.hxx.begin(), H.hxx.end(), hc.begin() + 3 * H.ncol);
     std::copy(H.hyy.begin(), H.hyy.end(), hc.begin() + 4 * H.ncol);
     if (e == cudaSuccess) e = cudaMemcpy(P->d_hcols, hc.data(), hc.size() * sizeof(double), cudaMemcpyHostToDevice);
-    // factors slot-major on the device, rows ordered colour, level, column:
-    // lu[s * m + (c * P + j + 1) * (ncol / 4) + q] for rank (c * ncol/4 + q) * P + j + 1
+    // factors slot-major on the device, rows ordered group, level, column:
+    // lu[s * m + goff[c] * P + (j + 1) * size(c) + q] for rank (goff[c] + q) * P + j + 1
     {
         std::vector<double> t((size_t)m * ns);
         std::vector<float> t32((size_t)m * ns);
-        const long long per = H.ncol / 4;
         for (long long i = 0; i < m; ++i) {
-            const long long c = i / (per * H.P), rem = i % (per * H.P), q = rem / H.P, a = rem % H.P;
-            const long long i2 = (c * H.P + a) * per + q;
+            const long long cr = i / H.P, a = i % H.P;
+            const int c = H.grp[H.gcol[cr]];
+            const long long per = H.goff[c + 1] - H.goff[c], q = cr - H.goff[c];
+            const long long i2 = (long long)H.goff[c] * H.P + a * per + q;
             for (int s = 0; s < ns; ++s) {
                 double v = lu_rows[(size_t)i * ns + s];
                 t[(size_t)s * m + i2] = v;
@@ -521,6 +635,14 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     Dev &D = P->dev;
     D.nx = g.nx; D.ny = g.ny; D.nz = g.nz; D.P = H.P; D.ncol = H.ncol; D.three_d = three_d;
     D.layout = H.layout; D.nslot = ns; D.m = m; D.dx = H.dx; D.dy = H.dy;
+    D.walls = H.walls;
+    D.ngroups = H.ngroups;
+    for (int c = 0; c <= H.ngroups; ++c) P->goff_h[c] = H.goff[c];
+    D.goff = P->d_goff;
+    D.gcol = P->d_gcol;
+    D.grp = P->d_grp;
+    D.wxo1 = P->d_weights + wxo_at;
+    D.wxo2 = P->d_weights + wxo_at + W * W;
     D.wx1 = P->d_weights; D.wx2 = P->d_weights + W; D.wy1 = P->d_weights + 2 * W; D.wy2 = P->d_weights + 3 * W;
     D.ws1 = P->d_weights + 4 * W; D.ws2 = P->d_weights + 4 * W + H.P * W;
     D.win = P->d_win;

@@ -16,14 +16,21 @@ namespace sw {
 // ---------------------------------------------------------------------------
 constexpr size_t SMEM_FIXED = (sizeof(SmemFixed) + 255) & ~size_t(255);
 
-template <typename TI>
+// WALLS selects the instantiation for wall-bounded grids, so the kernel of
+// periodic grids carries none of the wall code (and the other way round).
+template <typename TI, bool WALLS>
 __global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemFixed &S = *reinterpret_cast<SmemFixed *>(smem_raw);
     GridTeam tm(A.part, A.nb);
     double ph[PH_COUNT];
     for (int i = 0; i < PH_COUNT; ++i) ph[i] = 0.0;
-    solve_body<GridTeam, TI>(tm, D, A, S, smem_raw + SMEM_FIXED, ph);
+    solve_body<GridTeam, TI, WALLS ? 1 : 0>(tm, D, A, S, smem_raw + SMEM_FIXED, ph);
+}
+
+static const void *solve_kernel_for(bool mixed_precision, bool walls) {
+    if (mixed_precision) return walls ? (const void *)solve_kernel<float, true> : (const void *)solve_kernel<float, false>;
+    return walls ? (const void *)solve_kernel<double, true> : (const void *)solve_kernel<double, false>;
 }
 
 // ---------------------------------------------------------------------------
@@ -46,7 +53,7 @@ __global__ void __launch_bounds__(NTHREADS) ilu_fwd_kernel(Dev D, int c, const d
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int q = gw; q < (D.ncol >> 2); q += nw) ilu_fwd_column<double, double>(D, c, q, in, out, lane);
+    for (int q = gw; q < group_size(D, c); q += nw) ilu_fwd_column<double, double>(D, c, q, in, out, lane);
 }
 
 struct SketchUpd {
@@ -79,7 +86,7 @@ __global__ void __launch_bounds__(NTHREADS) ilu_bwd_kernel(Dev D, int c, double 
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int q = gw; q < (D.ncol >> 2); q += nw) ilu_bwd_column<double>(D, c, q, out, lane);
+    for (int q = gw; q < group_size(D, c); q += nw) ilu_bwd_column<double>(D, c, q, out, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -119,7 +126,7 @@ static bool mixed(const Problem *P) { return P->params.precision == SW_PRECISION
 int setup_solver_launch(Problem *P) {
     Tiling t = make_tiling(P->dev);
     size_t smem = solve_smem(P->dev, t);
-    const void *kern = mixed(P) ? (const void *)solve_kernel<float> : (const void *)solve_kernel<double>;
+    const void *kern = solve_kernel_for(mixed(P), P->dev.walls != 0);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "solve_kernel smem attribute");
     e = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -207,7 +214,7 @@ static int launch_solve(Problem *P, const double *ep, const double *ec, const do
         e = cudaEventRecord(P->ev[2 * evi], s);
         if (e != cudaSuccess) return cuda_fail(e, "event record");
     }
-    const void *kern = mixed(P) ? (const void *)solve_kernel<float> : (const void *)solve_kernel<double>;
+    const void *kern = solve_kernel_for(mixed(P), P->dev.walls != 0);
     e = cudaLaunchCooperativeKernel(kern, P->nblocks, NTHREADS, args, P->smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "solve launch");
     P->launches++;
@@ -352,13 +359,18 @@ extern "C" int sw_apply_preconditioner(sw_problem *pp, const double *v, double *
     Problem *P = (Problem *)pp;
     if (!P || !v || !out || v == out) { set_error("bad argument"); return SW_ERR_BAD_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
-    int per = P->ncol >> 2;
-    int blocks = (per * 32 + NTHREADS - 1) / NTHREADS;
-    for (int c = 0; c < 4; ++c) ilu_fwd_kernel<<<blocks, NTHREADS, 0, s>>>(P->dev, c, v, out);
-    for (int c = 3; c >= 0; --c) ilu_bwd_kernel<<<blocks, NTHREADS, 0, s>>>(P->dev, c, out);
+    const Dev &D = P->dev;
+    for (int c = 0; c < D.ngroups; ++c) {
+        int blocks = ((P->goff_h[c + 1] - P->goff_h[c]) * 32 + NTHREADS - 1) / NTHREADS;
+        ilu_fwd_kernel<<<blocks, NTHREADS, 0, s>>>(D, c, v, out);
+    }
+    for (int c = D.ngroups - 1; c >= 0; --c) {
+        int blocks = ((P->goff_h[c + 1] - P->goff_h[c]) * 32 + NTHREADS - 1) / NTHREADS;
+        ilu_bwd_kernel<<<blocks, NTHREADS, 0, s>>>(D, c, out);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "preconditioner launch");
-    P->launches += 8;
+    P->launches += 2 * D.ngroups;
     P->last_stream = s;
     return SW_OK;
 }

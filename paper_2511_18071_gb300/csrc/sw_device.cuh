@@ -39,6 +39,13 @@ enum {
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+// Walls: first column of the x window of an unknown of the linear system at
+// column ix (ghost columns included), and of surface data / velocities at the
+// physical column ixp (1..nx-2).  ixp of a ghost column is its wall column.
+__device__ __forceinline__ int xwin_field(const Dev &D, int ix) { return min(max(ix - HALF, 0), D.nx - W); }
+__device__ __forceinline__ int phys_col(const Dev &D, int ix) { return min(max(ix, 1), D.nx - 2); }
+__device__ __forceinline__ int xwin_phys(const Dev &D, int ixp) { return min(max(ixp - HALF, 1), D.nx - 1 - W); }
+
 // ---------------------------------------------------------------------------
 // a1: geometry.  For eta^(i-1) and eta^(i): d = h + eta, its surface
 // derivatives with the fixed 7-point operators (Sec. 3), and the per-column
@@ -49,16 +56,30 @@ __device__ inline void geometry_columns(const Dev &D, const double *eta_prev, co
     double *cc = D.gp;
     const int n = D.ncol;
     for (int c = tid; c < n; c += nth) {
-        int ix = c % D.nx, iy = c / D.nx;
+        // x window: centred and periodic, or (walls, 2-D) over the physical
+        // columns; a ghost column takes the coefficients of its wall column
+        int ix = c % D.nx;
+        const int iy = c / D.nx;
+        int xs0 = ix - HALF;
+        const double *w1 = D.wx1, *w2 = D.wx2;
+        if (D.walls) {
+            ix = phys_col(D, ix);
+            xs0 = xwin_phys(D, ix);
+            w1 = D.wxo1 + (ix - xs0) * W;
+            w2 = D.wxo2 + (ix - xs0) * W;
+        }
+        const int ce = iy * D.nx + ix;   // column the coefficients are evaluated at
         double dp1 = 0, dp2 = 0, dc1 = 0, dpy1 = 0, dpy2 = 0, dcy1 = 0;
 #pragma unroll
         for (int t = -HALF; t <= HALF; ++t) {
-            int cx = iy * D.nx + wrapi(ix + t, D.nx);
+            int gx = xs0 + t + HALF;
+            if (!D.walls) gx = wrapi(gx, D.nx);
+            int cx = iy * D.nx + gx;
             double vp = D.h[cx] + eta_prev[cx];
             double vc = D.h[cx] + eta_cur[cx];
-            dp1 += D.wx1[t + HALF] * vp;
-            dp2 += D.wx2[t + HALF] * vp;
-            dc1 += D.wx1[t + HALF] * vc;
+            dp1 += w1[t + HALF] * vp;
+            dp2 += w2[t + HALF] * vp;
+            dc1 += w1[t + HALF] * vc;
             if (D.three_d) {
                 int cy = wrapi(iy + t, D.ny) * D.nx + ix;
                 double wp = D.h[cy] + eta_prev[cy];
@@ -68,15 +89,16 @@ __device__ inline void geometry_columns(const Dev &D, const double *eta_prev, co
                 dcy1 += D.wy1[t + HALF] * wc;
             }
         }
-        double dp = D.h[c] + eta_prev[c], dcu = D.h[c] + eta_cur[c];
+        double dp = D.h[ce] + eta_prev[ce], dcu = D.h[ce] + eta_cur[ce];
         double f = 1.0 / dp, e = 1.0 / dcu;
-        double hx = D.hx[c], hy = D.three_d ? D.hy[c] : 0.0;
+        double hx = D.hx[ce], hy = D.three_d ? D.hy[ce] : 0.0;
+        const double hxx = D.hxx[ce], hyy = D.three_d ? D.hyy[ce] : 0.0;
         cc[CC_F * n + c] = f;
         cc[CC_E * n + c] = e;
         cc[CC_EF * n + c] = e * f;
         cc[CC_AP0 * n + c] = hx * f;
         cc[CC_AP1 * n + c] = dp1 * f;
-        cc[CC_AXP0 * n + c] = D.hxx[c] * f;
+        cc[CC_AXP0 * n + c] = hxx * f;
         cc[CC_AXP1 * n + c] = dp2 * f;
         cc[CC_BP0 * n + c] = hx * e;
         cc[CC_BP1 * n + c] = dc1 * e;
@@ -89,7 +111,7 @@ __device__ inline void geometry_columns(const Dev &D, const double *eta_prev, co
         if (D.three_d) {
             cc[CC_AY0 * n + c] = hy * f;
             cc[CC_AY1 * n + c] = dpy1 * f;
-            cc[CC_AYY0 * n + c] = D.hyy[c] * f;
+            cc[CC_AYY0 * n + c] = hyy * f;
             cc[CC_AYY1 * n + c] = dpy2 * f;
             cc[CC_BY0 * n + c] = hy * e;
             cc[CC_BY1 * n + c] = dcy1 * e;
@@ -104,6 +126,8 @@ __device__ inline void geometry_columns(const Dev &D, const double *eta_prev, co
 // Weights and per-column coefficients in the arithmetic precision of the caller.
 template <typename T> struct Prec;
 template <> struct Prec<double> {
+    __device__ static const double *wxo1(const Dev &D) { return D.wxo1; }
+    __device__ static const double *wxo2(const Dev &D) { return D.wxo2; }
     __device__ static const double *wx1(const Dev &D) { return D.wx1; }
     __device__ static const double *wx2(const Dev &D) { return D.wx2; }
     __device__ static const double *wy1(const Dev &D) { return D.wy1; }
@@ -113,6 +137,8 @@ template <> struct Prec<double> {
     __device__ static const double *cc(const Dev &D) { return D.gp; }
 };
 template <> struct Prec<float> {
+    __device__ static const float *wxo1(const Dev &D) { return D.w32 + 4 * W + 2 * D.P * W; }
+    __device__ static const float *wxo2(const Dev &D) { return D.w32 + 4 * W + 2 * D.P * W + W * W; }
     __device__ static const float *wx1(const Dev &D) { return D.w32; }
     __device__ static const float *wx2(const Dev &D) { return D.w32 + W; }
     __device__ static const float *wy1(const Dev &D) { return D.w32 + 2 * W; }
@@ -138,8 +164,8 @@ struct Tiling {
     int TX, TY, HX, HY, HW, ntx, nty, ntiles;
 };
 
-template <typename T, class Loader, class Store>
-__device__ inline void apply_tile(const Dev &D, const Tiling &tl, int tile, T *sp, T *sq, Loader &ld, Store &st) {
+template <typename T, bool WALLS, class Loader, class Store>
+__device__ inline void apply_tile_t(const Dev &D, const Tiling &tl, int tile, T *sp, T *sq, Loader &ld, Store &st) {
     const int P = D.P, HX = tl.HX, HY = tl.HY, HW = tl.HW;
     const int tx0 = (tile % tl.ntx) * tl.TX;
     const int ty0 = (tile / tl.ntx) * tl.TY;
@@ -151,8 +177,12 @@ __device__ inline void apply_tile(const Dev &D, const Tiling &tl, int tile, T *s
         bool hxo = a < HALF || a >= HX - HALF;
         bool hyo = D.three_d && (b < HALF || b >= HY - HALF);
         T v = T(0);
-        if (!(hxo && hyo)) {
-            int gx = wrapi(tx0 + a - HALF, D.nx);
+        int gx = tx0 + a - HALF;
+        if (WALLS) {
+            // no wrap: the shifted windows next to a wall never reach outside [0, nx)
+            if (gx >= 0 && gx < D.nx) v = ld((long long)l * D.ncol + gx);
+        } else if (!(hxo && hyo)) {
+            gx = wrapi(gx, D.nx);
             int gy = D.three_d ? wrapi(ty0 + b - HALF, D.ny) : 0;
             v = ld((long long)l * D.ncol + gy * D.nx + gx);
         }
@@ -182,15 +212,39 @@ __device__ inline void apply_tile(const Dev &D, const Tiling &tl, int tile, T *s
         int c = gy * D.nx + gx;
         int hr = b * HX + a;
         long long node = (long long)l * n + c;
+        // x window of the row: positions t = 0..6 at shared-memory offsets
+        // x0 + t from the row's column, weights of the evaluation point
+        int x0 = -HALF;
+        const T *wa1 = wx1, *wa2 = wx2;
+        if (WALLS) {
+            const int ixe = phys_col(D, gx);          // a ghost row evaluates at its wall column
+            const int xs = xwin_field(D, ixe);
+            x0 = xs - gx;
+            wa1 = Prec<T>::wxo1(D) + (ixe - xs) * W;
+            wa2 = Prec<T>::wxo2(D) + (ixe - xs) * W;
+        }
         T y;
         if (l == P - 1) {
             y = sp[l * HW + hr];
+        } else if (WALLS && (gx == 0 || gx == D.nx - 1)) {
+            // wall row (walls of Sec. 5.2, ghost nodes of Sec. 3): n . grad^(i-1) p at the wall
+            // node (iw, j) = +-(D_chi p + sigma_x^(i-1) D_sigma p); the ghost column holds the
+            // coefficients of its wall column
+            const int dw = gx == 0 ? 1 : -1;          // shared-memory offset of the wall column
+            T sg = T(l - 1) * inv_nzm1;
+            T aa = cc[CC_AP0 * n + c] - sg * cc[CC_AP1 * n + c];
+            const T *pl = sp + l * HW + hr + x0;
+            T px = T(0);
+#pragma unroll
+            for (int t = 0; t < W; ++t) px += wa1[t] * pl[t];
+            y = px + aa * sq[l * HW + hr + dw];
+            if (gx == 0) y = -y;
         } else if (l == 0) {
             // ghost row at the bed (level index 1)
             T px = T(0), py = T(0);
 #pragma unroll
             for (int t = -HALF; t <= HALF; ++t) {
-                px += wx1[t + HALF] * sp[HW + hr + t];
+                px += wa1[t + HALF] * sp[HW + hr + x0 + HALF + t];
                 if (D.three_d) py += wy1[t + HALF] * sp[HW + hr + t * HX];
             }
             y = cc[CC_GS * n + c] * sq[HW + hr] + cc[CC_GX * n + c] * px;
@@ -209,8 +263,8 @@ __device__ inline void apply_tile(const Dev &D, const Tiling &tl, int tile, T *s
             T pxx = T(0), pxs = T(0);
 #pragma unroll
             for (int t = -HALF; t <= HALF; ++t) {
-                pxx += wx2[t + HALF] * pl[t];
-                pxs += wx1[t + HALF] * ql[t];
+                pxx += wa2[t + HALF] * pl[x0 + HALF + t];
+                pxs += wa1[t + HALF] * ql[x0 + HALF + t];
             }
             const T *w2 = ws2 + l * W;
             const T *pc = sp + (D.win[l] + 1) * HW + hr;
@@ -241,15 +295,42 @@ __device__ inline void apply_tile(const Dev &D, const Tiling &tl, int tile, T *s
     __syncthreads();
 }
 
+// Wall mode of a caller: 0 periodic grids only, 1 walls only (both fixed at
+// compile time, so a kernel instantiated for one kind carries no code for the
+// other), 2 decided per problem at run time (batches mixing both).
+template <int WM>
+__device__ __forceinline__ bool walls_of(const Dev &D) { return WM == 2 ? D.walls != 0 : WM == 1; }
+
+template <typename T, int WM = 2, class Loader, class Store>
+__device__ inline void apply_tile(const Dev &D, const Tiling &tl, int tile, T *sp, T *sq, Loader &ld, Store &st) {
+    if (walls_of<WM>(D)) apply_tile_t<T, true>(D, tl, tile, sp, sq, ld, st);
+    else apply_tile_t<T, false>(D, tl, tile, sp, sq, ld, st);
+}
+
 // ---------------------------------------------------------------------------
-// a3: preconditioner sweeps.  Rank order = colour, column, level.  A warp
-// owns one column; lane l holds levels l-1 and l+31.  The forward sweep of
-// colour c first subtracts the couplings to columns of lower colours (final
-// already), then runs the in-column recurrence level by level, broadcasting
-// each new value with a shuffle.  The backward sweep mirrors it with the
-// upper factor and higher colours.  In place on `out`.
+// a3: preconditioner sweeps.  Rank order = column group, column, level.  A
+// warp owns one column; lane l holds levels l-1 and l+31.  The forward sweep
+// of group c first subtracts the couplings to columns of earlier groups
+// (final already), then applies the inverse of the column's unit-lower block.
+// The backward sweep mirrors it with the upper factor and later groups.  In
+// place on `out`.
 // ---------------------------------------------------------------------------
+// Column groups: periodic grids have four equal colours (closed form); with
+// walls the offsets come from the device table.
+template <bool WALLS>
+__device__ __forceinline__ int group_off(const Dev &D, int c) { return WALLS ? D.goff[c] : c * (D.ncol >> 2); }
+template <bool WALLS>
+__device__ __forceinline__ int group_size_t(const Dev &D, int c) {
+    return WALLS ? D.goff[c + 1] - D.goff[c] : (D.ncol >> 2);
+}
+template <int WM = 2>
+__device__ __forceinline__ int group_size(const Dev &D, int c) {
+    return walls_of<WM>(D) ? group_size_t<true>(D, c) : group_size_t<false>(D, c);
+}
+
+template <bool WALLS>
 __device__ __forceinline__ int col_of(const Dev &D, int c, int q) {
+    if (WALLS) return D.gcol[D.goff[c] + q];
     if (!D.three_d) return c + 4 * q;
     int per_row = D.nx >> 2;
     int iy = q / per_row;
@@ -330,9 +411,38 @@ template <> struct Off<BOX3D> {
     __device__ static constexpr int slot(int i) { return i < 42 ? (ox(i) + 3) * 7 + i % 7 : 49 + ((i - 42) / 7) * 7 + (i - 42) % 7; }
 };
 
-// Device row index of the factors: colour, level, column within the colour.
+// Device row index of the factors: group, level, column within the group.
+template <bool WALLS>
 __device__ __forceinline__ long long fac_row(const Dev &D, int c, int q, int j) {
-    return ((long long)c * D.P + (j + 1)) * (D.ncol >> 2) + q;
+    return (long long)group_off<WALLS>(D, c) * D.P + (long long)(j + 1) * group_size_t<WALLS>(D, c) + q;
+}
+
+// Walls (2-D): sum over the off-column slots of row (ix, j) whose column lies in
+// an earlier (LOWER) or later group.  Slots follow the x positions t of the
+// row's (possibly shifted) window; the own column sits at position o.
+template <typename T, bool LOWER>
+__device__ __forceinline__ T off_column_sum_walls(const Dev &D, const T *lu, const T *vals, int c, int ix, int j,
+                                                  long long r) {
+    const long long m = D.m;
+    const int xs = xwin_field(D, ix), o = ix - xs;
+    const int w0 = D.win[j + 1];
+    T acc = T(0);
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        if (t == o) continue;
+        const int nc = xs + t;
+        const int g = D.grp[nc];
+        if (LOWER ? (g >= c) : (g <= c)) continue;
+        if (D.layout == CROSS2D) {
+            const int s = t < o ? t : t - 1;
+            acc += lu[(long long)s * m + r] * vals[(long long)(j + 1) * D.ncol + nc];
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < W; ++kk)
+                acc += lu[(long long)(t * 7 + kk) * m + r] * vals[(long long)(w0 + kk + 1) * D.ncol + nc];
+        }
+    }
+    return acc;
 }
 
 // sum over the off-column slots whose neighbour colour satisfies pick(colour)
@@ -393,12 +503,19 @@ __device__ __forceinline__ void column_block_product(const T *bt, const T (&g)[2
 }
 
 // forward (lower) sweep of one column of colour c; in -> out
-template <int L, typename T, typename TI>
+template <int L, typename T, bool LOWER, bool WALLS>
+__device__ __forceinline__ T off_sum(const Dev &D, const T *lu, const T *vals, int c, int ix, int iy, int j,
+                                     long long r) {
+    if (WALLS) return off_column_sum_walls<T, LOWER>(D, lu, vals, c, ix, j, r);
+    return off_column_sum<L, T, LOWER>(D, lu, vals, c, ix, iy, j, r);
+}
+
+template <int L, typename T, typename TI, bool WALLS>
 __device__ inline void ilu_fwd_column_t(const Dev &D, int c, int q, const TI *in, T *out, int lane) {
     const T *lu = lu_ptr<T>(D);
-    const int col = col_of(D, c, q);
+    const int col = col_of<WALLS>(D, c, q);
     const int ix = col % D.nx, iy = col / D.nx;
-    const long long cr = (long long)c * (D.ncol >> 2) + q;
+    const long long cr = (long long)group_off<WALLS>(D, c) + q;
     T g[2], y[2];
     const int jl[2] = {lane - 1, lane + 31};
 #pragma unroll
@@ -407,7 +524,7 @@ __device__ inline void ilu_fwd_column_t(const Dev &D, int c, int q, const TI *in
         g[h] = T(0);
         if (j >= D.nz) continue;
         g[h] = T(in[(long long)(j + 1) * D.ncol + col]) -
-               off_column_sum<L, T, true>(D, lu, out, c, ix, iy, j, fac_row(D, c, q, j));
+               off_sum<L, T, true, WALLS>(D, lu, out, c, ix, iy, j, fac_row<WALLS>(D, c, q, j));
     }
     // in-column part: y = (unit lower block)^-1 g
     column_block_product<T>(linv_ptr<T>(D) + cr * D.P * D.P, g, y, D.P, lane);
@@ -417,12 +534,12 @@ __device__ inline void ilu_fwd_column_t(const Dev &D, int c, int q, const TI *in
 }
 
 // backward (upper) sweep of one column of colour c; in place on out
-template <int L, typename T>
+template <int L, typename T, bool WALLS>
 __device__ inline void ilu_bwd_column_t(const Dev &D, int c, int q, T *out, int lane) {
     const T *lu = lu_ptr<T>(D);
-    const int col = col_of(D, c, q);
+    const int col = col_of<WALLS>(D, c, q);
     const int ix = col % D.nx, iy = col / D.nx;
-    const long long cr = (long long)c * (D.ncol >> 2) + q;
+    const long long cr = (long long)group_off<WALLS>(D, c) + q;
     T g[2], x[2];
     const int jl[2] = {lane - 1, lane + 31};
 #pragma unroll
@@ -431,7 +548,7 @@ __device__ inline void ilu_bwd_column_t(const Dev &D, int c, int q, T *out, int 
         g[h] = T(0);
         if (j >= D.nz) continue;
         g[h] = out[(long long)(j + 1) * D.ncol + col] -
-               off_column_sum<L, T, false>(D, lu, out, c, ix, iy, j, fac_row(D, c, q, j));
+               off_sum<L, T, false, WALLS>(D, lu, out, c, ix, iy, j, fac_row<WALLS>(D, c, q, j));
     }
     __syncwarp();
     // in-column part: x = (upper block)^-1 g
@@ -445,29 +562,35 @@ __device__ inline void ilu_bwd_column_t(const Dev &D, int c, int q, T *out, int 
 // row (consecutive threads take consecutive columns of one level, so factor
 // reads are coalesced): g = rhs - (couplings to the other colours), stored in
 // place.  Phase 2, one warp per column: the in-column block product.
-template <int L, typename T, typename TI, bool LOWER>
+template <int L, typename T, typename TI, bool LOWER, bool WALLS>
 __device__ inline void ilu_gather_row_t(const Dev &D, int c, long long row, const TI *in, T *out) {
-    const int per = D.ncol >> 2;
+    const int per = group_size_t<WALLS>(D, c);
     const int q = (int)(row % per), j = (int)(row / per) - 1;
-    const int col = col_of(D, c, q);
+    const int col = col_of<WALLS>(D, c, q);
     const int ix = col % D.nx, iy = col / D.nx;
     const long long node = (long long)(j + 1) * D.ncol + col;
     const T rhs = LOWER ? T(in[node]) : out[node];
-    out[node] = rhs - off_column_sum<L, T, LOWER>(D, lu_ptr<T>(D), out, c, ix, iy, j, fac_row(D, c, q, j));
+    out[node] = rhs - off_sum<L, T, LOWER, WALLS>(D, lu_ptr<T>(D), out, c, ix, iy, j, fac_row<WALLS>(D, c, q, j));
 }
-template <typename T, typename TI, bool LOWER>
+template <typename T, typename TI, bool LOWER, int WM = 2>
 __device__ inline void ilu_gather_row(const Dev &D, int c, long long row, const TI *in, T *out) {
+    if (walls_of<WM>(D)) {
+        if (D.layout == CROSS2D) ilu_gather_row_t<CROSS2D, T, TI, LOWER, true>(D, c, row, in, out);
+        else ilu_gather_row_t<BOX2D, T, TI, LOWER, true>(D, c, row, in, out);
+        return;
+    }
     switch (D.layout) {
-    case CROSS2D: ilu_gather_row_t<CROSS2D, T, TI, LOWER>(D, c, row, in, out); break;
-    case BOX2D: ilu_gather_row_t<BOX2D, T, TI, LOWER>(D, c, row, in, out); break;
-    case CROSS3D: ilu_gather_row_t<CROSS3D, T, TI, LOWER>(D, c, row, in, out); break;
-    default: ilu_gather_row_t<BOX3D, T, TI, LOWER>(D, c, row, in, out); break;
+    case CROSS2D: ilu_gather_row_t<CROSS2D, T, TI, LOWER, false>(D, c, row, in, out); break;
+    case BOX2D: ilu_gather_row_t<BOX2D, T, TI, LOWER, false>(D, c, row, in, out); break;
+    case CROSS3D: ilu_gather_row_t<CROSS3D, T, TI, LOWER, false>(D, c, row, in, out); break;
+    default: ilu_gather_row_t<BOX3D, T, TI, LOWER, false>(D, c, row, in, out); break;
     }
 }
-template <typename T>
+template <typename T, int WM = 2>
 __device__ inline void ilu_column_product(const Dev &D, int c, int q, T *out, int lane, bool upper) {
-    const int col = col_of(D, c, q);
-    const long long cr = (long long)c * (D.ncol >> 2) + q;
+    const bool wl = walls_of<WM>(D);
+    const int col = wl ? col_of<true>(D, c, q) : col_of<false>(D, c, q);
+    const long long cr = (long long)(wl ? group_off<true>(D, c) : group_off<false>(D, c)) + q;
     T g[2], y[2];
     const int jl[2] = {lane - 1, lane + 31};
 #pragma unroll
@@ -481,22 +604,32 @@ __device__ inline void ilu_column_product(const Dev &D, int c, int q, T *out, in
 }
 
 // runtime dispatch on the layout
-template <typename T, typename TI>
+template <typename T, typename TI, int WM = 2>
 __device__ inline void ilu_fwd_column(const Dev &D, int c, int q, const TI *in, T *out, int lane) {
+    if (walls_of<WM>(D)) {
+        if (D.layout == CROSS2D) ilu_fwd_column_t<CROSS2D, T, TI, true>(D, c, q, in, out, lane);
+        else ilu_fwd_column_t<BOX2D, T, TI, true>(D, c, q, in, out, lane);
+        return;
+    }
     switch (D.layout) {
-    case CROSS2D: ilu_fwd_column_t<CROSS2D, T, TI>(D, c, q, in, out, lane); break;
-    case BOX2D: ilu_fwd_column_t<BOX2D, T, TI>(D, c, q, in, out, lane); break;
-    case CROSS3D: ilu_fwd_column_t<CROSS3D, T, TI>(D, c, q, in, out, lane); break;
-    default: ilu_fwd_column_t<BOX3D, T, TI>(D, c, q, in, out, lane); break;
+    case CROSS2D: ilu_fwd_column_t<CROSS2D, T, TI, false>(D, c, q, in, out, lane); break;
+    case BOX2D: ilu_fwd_column_t<BOX2D, T, TI, false>(D, c, q, in, out, lane); break;
+    case CROSS3D: ilu_fwd_column_t<CROSS3D, T, TI, false>(D, c, q, in, out, lane); break;
+    default: ilu_fwd_column_t<BOX3D, T, TI, false>(D, c, q, in, out, lane); break;
     }
 }
-template <typename T>
+template <typename T, int WM = 2>
 __device__ inline void ilu_bwd_column(const Dev &D, int c, int q, T *out, int lane) {
+    if (walls_of<WM>(D)) {
+        if (D.layout == CROSS2D) ilu_bwd_column_t<CROSS2D, T, true>(D, c, q, out, lane);
+        else ilu_bwd_column_t<BOX2D, T, true>(D, c, q, out, lane);
+        return;
+    }
     switch (D.layout) {
-    case CROSS2D: ilu_bwd_column_t<CROSS2D, T>(D, c, q, out, lane); break;
-    case BOX2D: ilu_bwd_column_t<BOX2D, T>(D, c, q, out, lane); break;
-    case CROSS3D: ilu_bwd_column_t<CROSS3D, T>(D, c, q, out, lane); break;
-    default: ilu_bwd_column_t<BOX3D, T>(D, c, q, out, lane); break;
+    case CROSS2D: ilu_bwd_column_t<CROSS2D, T, false>(D, c, q, out, lane); break;
+    case BOX2D: ilu_bwd_column_t<BOX2D, T, false>(D, c, q, out, lane); break;
+    case CROSS3D: ilu_bwd_column_t<CROSS3D, T, false>(D, c, q, out, lane); break;
+    default: ilu_bwd_column_t<BOX3D, T, false>(D, c, q, out, lane); break;
     }
 }
 

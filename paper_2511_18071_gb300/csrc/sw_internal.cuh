@@ -16,9 +16,13 @@ constexpr int MAX_LEVELS = 64;      // nz + 1 <= 64 (two levels per lane in the 
 constexpr int MAX_RESTART = 32;
 constexpr int MAX_K = 16;
 
-// Sparsity layouts of the preconditioner rows ("slots").
-//   CROSS2D: x neighbours at the row's own level (6), sigma window (7)        -> 13
-//   BOX2D:   (dx, window level) for dx in -3..3 (7 x 7)                        -> 49
+// Sparsity layouts of the preconditioner rows ("slots").  An x position t =
+// 0..6 is the t-th column of the row's 7-column x window (t = dx + 3 when
+// the window is centred; next to a wall the window is shifted and the row's
+// own column sits at position o != 3).
+//   CROSS2D: x positions other than the own column at the row's level (6),
+//            sigma window of the own column (7)                                -> 13
+//   BOX2D:   (x position, window level) (7 x 7); own column at position o      -> 49
 //   CROSS3D: x (6) and y (6) neighbours at the own level, sigma window (7)     -> 19
 //   BOX3D:   x box (7 x 7) and y box without its centre column (6 x 7)         -> 91
 enum Layout { CROSS2D = 0, BOX2D = 1, CROSS3D = 2, BOX3D = 3 };
@@ -26,23 +30,42 @@ enum Layout { CROSS2D = 0, BOX2D = 1, CROSS3D = 2, BOX3D = 3 };
 __host__ __device__ inline int layout_nslot(int L) {
     return L == CROSS2D ? 13 : L == BOX2D ? 49 : L == CROSS3D ? 19 : 91;
 }
-// Slot holding the sigma-window entry kk (same column).
+// Slot holding the sigma-window entry kk (same column) of a row with a centred x window.
 __host__ __device__ inline int sigma_slot(int L, int kk) {
     return (L == CROSS2D ? 6 : L == CROSS3D ? 12 : 21) + kk;
 }
+// The same for a row whose own column is at x position o (2-D layouts).
+__host__ __device__ inline int own_slot(int L, int kk, int o) {
+    return L == BOX2D ? o * 7 + kk : sigma_slot(L, kk);
+}
+
+constexpr int MAX_GROUPS = 7;   // column groups of the ILU sweeps: 4 colours (+3 next to walls)
 
 // Device view of one problem (plain pointers; passed to kernels by value).
 struct Dev {
     int nx, ny, nz, P, ncol, three_d, layout, nslot;
     long long m;
     double dx, dy;
+    // Walls (2-D): ghost columns 0 and nx-1 outside the walls, x windows
+    // shifted inside the grid next to them (see include/sawave.h).
+    int walls;
+    // ILU column groups in sweep order; columns of one group are uncoupled.
+    // Periodic: colour (ix + iy) mod 4.  Walls: colours ix mod 4 of columns
+    // 3..nx-4, then {0, nx-1}, {1, nx-2}, {2, nx-3}.
+    int ngroups;
+    const int *goff;                       // walls: first column rank of each group (ngroups + 1);
+                                           // periodic groups are the four equal colours
+    const int *gcol;                       // walls: column of each column rank (ncol)
+    const unsigned char *grp;              // walls: group of each column (ncol)
     const double *wx1, *wx2, *wy1, *wy2;   // 7 each
+    const double *wxo1, *wxo2;             // walls: 7 x 7 each, weights at node o of a 7-node window
     const double *ws1, *ws2;               // P x 7, row j+1
     const int *win;                        // P, first level of the sigma window of level j
     const double *h, *hx, *hy, *hxx, *hyy; // ncol
     double *gp;                            // per-column coefficients of the current geometry pair
     float *gp32;                           // the same in FP32 (for the FP32 operator; may be null)
-    const float *w32;                      // weights in FP32: wx1, wx2, wy1, wy2 (7 each), ws1, ws2 (P x 7)
+    const float *w32;                      // weights in FP32: wx1, wx2, wy1, wy2 (7 each), ws1, ws2 (P x 7),
+                                           // wxo1, wxo2 (7 x 7 each)
     const double *lu64;                    // nslot x m (rank-major), FP64 factors
     const float *lu32;                     // same, FP32 copy (mixed precision)
     const double *udinv64;                 // 1 / u_jj per rank
@@ -95,6 +118,14 @@ struct Problem {
     double *d_p = nullptr, *d_rhs = nullptr, *d_eta_new = nullptr, *d_feta = nullptr;
     double *d_drv = nullptr;       // driver scratch (several fields)
     double *d_host_io = nullptr;   // staging for the host-buffer entry point
+    int *d_gcol = nullptr;         // walls: column order of the ILU sweeps
+    int *d_goff = nullptr;         // walls: group offsets (device copy of goff_h)
+    int goff_h[MAX_GROUPS + 1] = {};   // first column rank of each group (host)
+    unsigned char *d_grp = nullptr;
+    bool relax_on = false;         // generation/absorption zones after each stage
+    sw_relaxation relax{};
+    double relax_k = 0.0;          // wavenumber of the incident wave
+    long long step_index = 0;      // completed Runge-Kutta steps since sw_set_state
     int ybuf = 0;                  // which sketch buffer holds Y
     bool pending = false;          // Y still lacks the newest solution (folded in by the next solve)
     long long n_solves = 0;

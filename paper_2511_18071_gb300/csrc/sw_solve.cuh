@@ -176,48 +176,51 @@ struct StResid {
     }
 };
 
-template <class Team, typename TC, class L, class S>
+template <class Team, typename TC, int WM, class L, class S>
 __device__ inline void team_apply(Team &tm, const Dev &D, const Tiling &tl, void *smem_tiles, L &ld, S &st) {
     TC *sp = reinterpret_cast<TC *>(smem_tiles);
     TC *sq = sp + (size_t)D.P * tl.HW;
-    for (int tile = tm.bid; tile < tl.ntiles; tile += tm.nb) apply_tile<TC>(D, tl, tile, sp, sq, ld, st);
+    for (int tile = tm.bid; tile < tl.ntiles; tile += tm.nb) apply_tile<TC, WM>(D, tl, tile, sp, sq, ld, st);
 }
 
-// out = U^-1 L^-1 in by colour sweeps; the last barrier is included.
-template <class Team, typename TI, typename TIn>
+// out = U^-1 L^-1 in by column-group sweeps; the last barrier is included.
+template <class Team, typename TI, typename TIn, int WM>
 __device__ inline void team_ilu(Team &tm, const Dev &D, const TIn *in, TI *out) {
     const int lane = threadIdx.x & 31;
     const int gw = tm.bid * NWARPS + (threadIdx.x >> 5);
     const int nw = tm.nb * NWARPS;
-    const int per = D.ncol >> 2;
-    if (per > 4 * nw) {
+    const int ng = WM == 0 ? 4 : D.ngroups;   // periodic grids: the four colours
+    if (group_size<WM>(D, 0) > 4 * nw) {
         // large problem: row-parallel coupling gathers, then per-column products
-        const long long rows = (long long)per * D.P;
         const long long tid = (long long)tm.bid * NTHREADS + threadIdx.x, nth = (long long)tm.nb * NTHREADS;
-        for (int c = 0; c < 4; ++c) {
-            for (long long r = tid; r < rows; r += nth) ilu_gather_row<TI, TIn, true>(D, c, r, in, out);
+        for (int c = 0; c < ng; ++c) {
+            const int per = group_size<WM>(D, c);
+            const long long rows = (long long)per * D.P;
+            for (long long r = tid; r < rows; r += nth) ilu_gather_row<TI, TIn, true, WM>(D, c, r, in, out);
             tm.sync();
-            for (int q = gw; q < per; q += nw) ilu_column_product<TI>(D, c, q, out, lane, false);
+            for (int q = gw; q < per; q += nw) ilu_column_product<TI, WM>(D, c, q, out, lane, false);
             tm.sync();
         }
-        for (int c = 3; c >= 0; --c) {
-            if (c < 3) {
-                for (long long r = tid; r < rows; r += nth) ilu_gather_row<TI, TI, false>(D, c, r, out, out);
+        for (int c = ng - 1; c >= 0; --c) {
+            const int per = group_size<WM>(D, c);
+            const long long rows = (long long)per * D.P;
+            if (c < ng - 1) {
+                for (long long r = tid; r < rows; r += nth) ilu_gather_row<TI, TI, false, WM>(D, c, r, out, out);
                 tm.sync();
             }
-            for (int q = gw; q < per; q += nw) ilu_column_product<TI>(D, c, q, out, lane, true);
+            for (int q = gw; q < per; q += nw) ilu_column_product<TI, WM>(D, c, q, out, lane, true);
             tm.sync();
         }
         return;
     }
-    for (int c = 0; c < 4; ++c) {
-        for (int q = gw; q < per; q += nw) ilu_fwd_column<TI, TIn>(D, c, q, in, out, lane);
-        if (c < 3) tm.sync();
+    for (int c = 0; c < ng; ++c) {
+        const int per = group_size<WM>(D, c);
+        for (int q = gw; q < per; q += nw) ilu_fwd_column<TI, TIn, WM>(D, c, q, in, out, lane);
+        if (c < ng - 1) tm.sync();
     }
-    for (int q = gw; q < per; q += nw) ilu_bwd_column<TI>(D, 3, q, out, lane);
-    tm.sync();
-    for (int c = 2; c >= 0; --c) {
-        for (int q = gw; q < per; q += nw) ilu_bwd_column<TI>(D, c, q, out, lane);
+    for (int c = ng - 1; c >= 0; --c) {
+        const int per = group_size<WM>(D, c);
+        for (int q = gw; q < per; q += nw) ilu_bwd_column<TI, WM>(D, c, q, out, lane);
         tm.sync();
     }
 }
@@ -280,7 +283,7 @@ __device__ inline void warp_fwdsub_t(const double *U, const double *rhs, double 
 // ---------------------------------------------------------------------------
 // The solve body.
 // ---------------------------------------------------------------------------
-template <class Team, typename TI>
+template <class Team, typename TI, int WM>
 __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed &S, void *tiles, double *ph) {
     const long long m = D.m;
     const int nb = tm.nb;
@@ -316,7 +319,7 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
     tick(PH_GEOM);
 
     // reference norms ||b|| and ||M^-1 b||
-    team_ilu<Team, TI, double>(tm, D, A.b, tw);
+    team_ilu<Team, TI, double, WM>(tm, D, A.b, tw);
     {
         double v[32];
 #pragma unroll
@@ -350,10 +353,10 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
                 StVec<double, double> st{Wm + (size_t)c * m};
                 if (upd) {
                     LdEwma<double, double> ld{Yc, A.xprev, A.decay, A.omega[c]};
-                    team_apply<Team, double>(tm, D, A.tl, tiles, ld, st);
+                    team_apply<Team, double, WM>(tm, D, A.tl, tiles, ld, st);
                 } else {
                     LdVec<double, double> ld{Yc, 1.0};
-                    team_apply<Team, double>(tm, D, A.tl, tiles, ld, st);
+                    team_apply<Team, double, WM>(tm, D, A.tl, tiles, ld, st);
                 }
             }
         }
@@ -512,14 +515,14 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
             {
                 StResid st{A.b, A.r, 0.0};
                 LdVec<double, double> ld{A.x, 1.0};
-                team_apply<Team, double>(tm, D, A.tl, tiles, ld, st);
+                team_apply<Team, double, WM>(tm, D, A.tl, tiles, ld, st);
                 double v[32];
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = 0.0;
                 v[0] = st.acc;
                 tm.sync();
                 tick(PH_RES_APPLY);
-                team_ilu<Team, TI, double>(tm, D, A.r, V);
+                team_ilu<Team, TI, double, WM>(tm, D, A.r, V);
                 for (long long p = tid; p < m; p += nth) {
                     const double vv = (double)V[p];
                     v[1] += vv * vv;
@@ -552,10 +555,10 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
                 {
                     LdVec<TI, TI> ld{V + (size_t)j * m, TI(S.scale[j])};
                     StVec<TI, TI> st{tw};
-                    team_apply<Team, TI>(tm, D, A.tl, tiles, ld, st);
+                    team_apply<Team, TI, WM>(tm, D, A.tl, tiles, ld, st);
                     tm.sync();
                     tick(PH_ARN_APPLY);
-                    team_ilu<Team, TI, TI>(tm, D, tw, w);
+                    team_ilu<Team, TI, TI, WM>(tm, D, tw, w);
                     tick(PH_ARN_ILU);
                 }
                 // CGS2 pass 1: d_i = V_i . w
@@ -760,7 +763,7 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
     {
         StResid st{A.b, A.r, 0.0};
         LdVec<double, double> ld{A.x, 1.0};
-        team_apply<Team, double>(tm, D, A.tl, tiles, ld, st);
+        team_apply<Team, double, WM>(tm, D, A.tl, tiles, ld, st);
         double v[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = 0.0;
