@@ -44,9 +44,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--members", type=int, default=512, help="batch512: number of instances")
-    ap.add_argument("--workload", default="stokes512", choices=["stokes512", "bumpy3d", "batch512"],
+    ap.add_argument("--spinup", type=int, default=800, help="flume2048: steps from rest before timing")
+    ap.add_argument("--workload", default="stokes512",
+                    choices=["stokes512", "bumpy3d", "batch512", "flume2048", "decay_sweep"],
                     help="stokes512: the headline 512 x 17 steep wave (FP64); bumpy3d: 256 x 256 x 17 "
-                         "precision form vs FP64; batch512: 512 uneven instances, batched vs one by one")
+                         "precision form vs FP64; batch512: 512 uneven instances, batched vs one by one; "
+                         "flume2048: 2048 x 17 flume over the bar with walls and relaxation zones (FP64); "
+                         "decay_sweep: the headline workload with EWMA decay r in {0.8, 0.9, 0.95, 1.0}")
     return ap.parse_args()
 
 
@@ -526,8 +530,102 @@ def batch512_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def flume2048_arm(args):
+    """2048 x 17 flume over the trapezoidal bar, walls and relaxation zones: EWMA vs previous vs cold.
+
+    The flume is spun up from rest (--spinup steps, past the ramp of the incident
+    wave) with the EWMA solver; the other guesses continue from the same saved
+    state and time."""
+    import torch
+
+    import __graft_entry__ as ge
+    import workloads as W
+    ge.build()
+    import paper_2511_18071_gb300 as sw
+    dev = torch.device("cuda", 0)
+    wl = W.flume_2d()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make(guess):
+        P = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], walls=True, **solver_kw(args, guess))
+        sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+        sw.set_relaxation(P.handle, wl["relax"])
+        return P
+
+    P = make("ewma")
+    sw.set_state(P.handle, _t(torch, dev, wl["u"]), None, _t(torch, dev, wl["w"]), _t(torch, dev, wl["eta"]))
+    run_steps(sw, torch, P, args.spinup)
+    torch.cuda.synchronize()
+    u = torch.empty(P.m, dtype=torch.float64, device=dev)
+    w = torch.empty_like(u)
+    eta = torch.empty(P.ncol, dtype=torch.float64, device=dev)
+    sw.get_state(P.handle, u=u, w=w, eta=eta)
+    torch.cuda.synchronize()
+    eta_max = float(eta.abs().max())
+    with ClockSampler(0) as clk:
+        res = {"ewma": _timed_steps(sw, torch, P, args.steps, flush)}
+    P.close()
+    for guess in ("previous", "cold"):
+        Q = make(guess)
+        sw.set_state(Q.handle, u, None, w, eta)
+        sw.set_step(Q.handle, args.spinup)
+        run_steps(sw, torch, Q, 1)
+        torch.cuda.synchronize()
+        res[guess] = _timed_steps(sw, torch, Q, args.plain_steps, flush)
+        Q.close()
+    ew = res["ewma"]
+    slim = lambda r: {k: r[k] for k in ("value", "iters_per_solve", "ms_per_step", "phase_us_per_solve")}
+    line = {"metric": METRIC, "value": ew["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.spinup, "ms_per_step": ew["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "iters_per_solve": ew["iters_per_solve"],
+            "previous": slim(res["previous"]), "plain": slim(res["cold"]),
+            "speedup_vs_plain": ew["value"] / res["cold"]["value"],
+            "speedup_vs_previous": ew["value"] / res["previous"]["value"], "eta_max_m": eta_max,
+            "clocks": clk.summary(), "phase_us_per_solve": ew["phase_us_per_solve"],
+            "config": {"workload": wl["name"], "unknowns": wl["m"], "lx_m": wl["lx"], "walls": True,
+                       "generation_zone_m": [wl["relax"]["gen_x0"], wl["relax"]["gen_x1"]],
+                       "absorption_zone_m": [wl["relax"]["abs_x0"], wl["relax"]["abs_x1"]],
+                       "wave": {"H_m": wl["relax"]["height"], "T_s": wl["relax"]["period"]}, "dt": wl["dt"],
+                       "guess": "ewma", "k": args.k, "decay": args.decay, "tol": 1e-8, "restart": 20,
+                       "l2": "flushed between timed steps (256 MiB write, outside the step events)"}}
+    print(json.dumps(line), flush=True)
+
+
+def decay_sweep_arm(args):
+    """EWMA forgetting rate r on the headline trajectory (the paper's decay study)."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2511_18071_gb300 as sw
+    dev = torch.device("cuda", 0)
+    wl = workload()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for r in (0.8, 0.9, 0.95, 1.0):
+        a = argparse.Namespace(**dict(vars(args), decay=r))
+        P = _make(sw, torch, dev, wl, "ewma", "fp64", a)
+        run_steps(sw, torch, P, args.warmup)
+        torch.cuda.synchronize()
+        res = _timed_steps(sw, torch, P, args.steps, flush)
+        out[str(r)] = {k: res[k] for k in ("value", "iters_per_solve", "ms_per_step")}
+        P.close()
+    best = max(out, key=lambda r: out[r]["value"])
+    line = {"metric": METRIC, "value": out["0.9"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "by_decay": out, "best_decay": float(best),
+            "config": {"workload": WORKLOAD, "guess": "ewma", "k": args.k, "tol": 1e-8, "restart": 20}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "flume2048":
+        flume2048_arm(args)
+        return
+    if args.workload == "decay_sweep":
+        decay_sweep_arm(args)
+        return
     if args.workload == "bumpy3d":
         bumpy3d_arm(args)
         return

@@ -200,6 +200,10 @@ int sw_advance_stage(sw_problem *p, void *stream);
  * them.  Copied.  SW_ERR_BAD_ARG for a 3-D problem or a non-positive period,
  * height or depth when a generation zone is set. */
 int sw_set_relaxation(sw_problem *p, const sw_relaxation *relax);
+/* Set the number of completed Runge-Kutta steps n (the next stage is stage 1
+ * of step n + 1, at time n dt), e.g. to continue a run from a saved state.
+ * Call between steps.  SW_ERR_BAD_ARG for n < 0. */
+int sw_set_step(sw_problem *p, long long n_steps);
 /* The system A(eta_prev, eta_cur) p = b of the last stage (copies; any pointer may be NULL). */
 int sw_get_last_system(sw_problem *p, double *d_eta_prev, double *d_eta_cur, double *d_b, void *stream);
 

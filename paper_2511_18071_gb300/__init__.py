@@ -14,7 +14,7 @@ from . import build as _build
 __all__ = ["Grid", "Params", "Stats", "Physics", "Problem", "create_problem", "destroy_problem", "problem_size",
            "solve_poisson", "solve_poisson_host", "get_stats", "apply_operator", "apply_preconditioner",
            "subspace_guess", "apply_operator_noalloc", "get_sketch", "set_sketch", "draw_omega", "set_physics", "set_state", "get_state",
-           "advance_stage", "set_relaxation", "Relaxation", "create_batch", "destroy_batch", "batch_solve", "batch_advance_stage", "Batch",
+           "advance_stage", "set_relaxation", "set_step", "Relaxation", "create_batch", "destroy_batch", "batch_solve", "batch_advance_stage", "Batch",
            "get_last_system", "get_phase_times", "enable_timing", "get_solve_time", "library_path", "SawaveError", "GUESS",
            "PRECISION"]
 
@@ -95,6 +95,7 @@ def lib():
         L.sw_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.sw_advance_stage.argtypes = [vp, vp]
         L.sw_set_relaxation.argtypes = [vp, C.POINTER(Relaxation)]
+        L.sw_set_step.argtypes = [vp, C.c_longlong]
         L.sw_enable_timing.argtypes = [vp, ip]
         L.sw_get_last_system.argtypes = [vp, vp, vp, vp, vp]
         L.sw_apply_operator_noalloc.argtypes = [C.POINTER(Grid), vp, vp, vp, vp, vp, vp]
@@ -110,7 +111,8 @@ def lib():
                      "sw_subspace_guess", "sw_get_sketch", "sw_set_sketch", "sw_draw_omega", "sw_set_physics",
                      "sw_set_state", "sw_get_state", "sw_advance_stage", "sw_enable_timing", "sw_get_solve_time",
                      "sw_get_last_system", "sw_apply_operator_noalloc", "sw_get_phase_times", "sw_create_batch",
-                     "sw_destroy_batch", "sw_batch_solve", "sw_batch_advance_stage", "sw_set_relaxation"]:
+                     "sw_destroy_batch", "sw_batch_solve", "sw_batch_advance_stage", "sw_set_relaxation",
+                     "sw_set_step"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -246,6 +248,10 @@ def set_relaxation(p, relax):
         return _check(lib().sw_set_relaxation(p, None))
     rl = relax if isinstance(relax, Relaxation) else Relaxation(**relax)
     return _check(lib().sw_set_relaxation(p, C.byref(rl)))
+
+
+def set_step(p, n_steps):
+    return _check(lib().sw_set_step(p, int(n_steps)))
 
 
 def get_last_system(p, eta_prev=None, eta_cur=None, b=None, stream=None):

@@ -221,3 +221,11 @@ extern "C" int sw_set_relaxation(sw_problem *pp, const sw_relaxation *rl) {
     P->relax_on = true;
     return SW_OK;
 }
+
+extern "C" int sw_set_step(sw_problem *pp, long long n_steps) {
+    Problem *P = (Problem *)pp;
+    if (!P || n_steps < 0) { set_error("bad argument"); return SW_ERR_BAD_ARG; }
+    P->step_index = n_steps;
+    P->stage = 0;
+    return SW_OK;
+}
