@@ -477,7 +477,36 @@ template <> __device__ __forceinline__ const float *uinv_ptr<float>(const Dev &D
 // y = B g for the column's P x P block inverse B (transposed storage bt[a2 * P + a]),
 // g held one level per lane (two slots per lane when P > 32).
 template <typename T>
+__device__ __forceinline__ void column_block_product_two(const T *bt, const T (&g)[2], T (&y)[2], int P, int lane);
+template <typename T>
 __device__ __forceinline__ void column_block_product(const T *bt, const T (&g)[2], T (&y)[2], int P, int lane) {
+    if (P > 32) {
+        column_block_product_two<T>(bt, g, y, P, lane);
+        return;
+    }
+    // One level per lane.  Predicated-off FP64 instructions still take their
+    // issue slots on this GPU, so the second half (levels 32..63) is not
+    // issued at all here: half the multiply-adds of the general form.
+    T a0 = T(0), a1 = T(0);
+    const bool on = lane < P;
+    int a2 = 0;
+    for (; a2 + 1 < P; a2 += 2) {
+        const T g0 = __shfl_sync(0xffffffffu, g[0], a2);
+        const T g1 = __shfl_sync(0xffffffffu, g[0], a2 + 1);
+        if (on) {
+            a0 += bt[a2 * P + lane] * g0;
+            a1 += bt[(a2 + 1) * P + lane] * g1;
+        }
+    }
+    if (a2 < P) {
+        const T g0 = __shfl_sync(0xffffffffu, g[0], a2);
+        if (on) a0 += bt[a2 * P + lane] * g0;
+    }
+    y[0] = a0 + a1;
+    y[1] = T(0);
+}
+template <typename T>
+__device__ __forceinline__ void column_block_product_two(const T *bt, const T (&g)[2], T (&y)[2], int P, int lane) {
     T a0[2] = {T(0), T(0)}, a1[2] = {T(0), T(0)};
     const int a_h[2] = {lane, lane + 32};
     int a2 = 0;

@@ -187,7 +187,10 @@ __device__ inline void team_apply(Team &tm, const Dev &D, const Tiling &tl, void
 template <class Team, typename TI, typename TIn, int WM>
 __device__ inline void team_ilu(Team &tm, const Dev &D, const TIn *in, TI *out) {
     const int lane = threadIdx.x & 31;
-    const int gw = tm.bid * NWARPS + (threadIdx.x >> 5);
+    // warp-major numbering: a group with fewer columns than blocks gets one
+    // warp on each of as many SMs, instead of all warps of a few SMs sharing
+    // their FP64 pipes and load units
+    const int gw = (threadIdx.x >> 5) * tm.nb + tm.bid;
     const int nw = tm.nb * NWARPS;
     const int ng = WM == 0 ? 4 : D.ngroups;   // periodic grids: the four colours
     if (group_size<WM>(D, 0) > 4 * nw) {
