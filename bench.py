@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--members", type=int, default=512, help="batch512: number of instances")
     ap.add_argument("--spinup", type=int, default=800, help="flume2048: steps from rest before timing")
+    ap.add_argument("--executor", default="auto", choices=["auto", "persistent", "streamed"],
+                    help="how a solve runs: auto (by size), persistent kernel, or streamed kernels")
     ap.add_argument("--workload", default="stokes512",
                     choices=["stokes512", "bumpy3d", "batch512", "flume2048", "decay_sweep"],
                     help="stokes512: the headline 512 x 17 steep wave (FP64); bumpy3d: 256 x 256 x 17 "
@@ -61,7 +63,7 @@ def workload():
 
 def solver_kw(args, guess):
     return dict(restart=20, max_restarts=500, tol=1e-8, guess=guess, k=args.k, decay=args.decay, n_init_solves=30,
-                seed=2511)
+                seed=2511, executor=getattr(args, "executor", "auto"))
 
 
 # ---------------------------------------------------------------------------
@@ -466,6 +468,7 @@ def bumpy3d_arm(args):
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": ach / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None, "traffic": None},
             "config": {"workload": "bumpy3d_256x256x17", "unknowns": wl["m"], "guess": "ewma", "k": args.k,
+                       "executor": args.executor,
                        "decay": args.decay, "tol": 1e-8, "restart": 20,
                        "l2": "inputs larger than L2 and flushed between timed steps"}}
     print(json.dumps(line), flush=True)

@@ -64,6 +64,15 @@ extern "C" {
 #define SW_PRECISION_FP64 0  /* every step in FP64 */
 #define SW_PRECISION_MIXED 1 /* FP32 inner GMRES cycles, FP64 outer residual */
 
+#define SW_EXEC_AUTO 0        /* persistent below SW_EXEC_STREAMED_MIN unknowns, streamed above */
+#define SW_EXEC_PERSISTENT 1  /* one cooperative kernel per solve, one block per SM: no host round
+                                 trip inside a solve, lowest latency for small problems */
+#define SW_EXEC_STREAMED 2    /* one high-occupancy kernel per phase, small control kernels in
+                                 between, one stream synchronisation per restart cycle: keeps HBM
+                                 busy on large problems (sw_solve_poisson then returns once the
+                                 solve has finished) */
+#define SW_EXEC_STREAMED_MIN 262144
+
 typedef struct sw_problem sw_problem;
 
 typedef struct {
@@ -83,6 +92,7 @@ typedef struct {
     int n_init_solves;  /* solves run with the previous-solution guess before EWMA starts (N_init, Sec. 5.1) */
     int precision;      /* SW_PRECISION_* */
     uint64_t seed;      /* seed of the Gaussian sketch vectors omega */
+    int executor;       /* SW_EXEC_*: how a solve is run on the GPU (same arithmetic) */
 } sw_params;
 
 typedef struct {

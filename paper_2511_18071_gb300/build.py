@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsawave.so")
-SOURCES = ["setup.cu", "solver.cu", "driver.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["setup.cu", "solver.cu", "driver.cu", "batch.cu", "noalloc.cu", "streamed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-Xcompiler", "-pthread", "--expt-relaxed-constexpr"]

@@ -413,8 +413,9 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     }
     if (p.restart < 1 || p.restart > MAX_RESTART || p.max_restarts < 0 || !(p.tol > 0) || p.guess < 0 ||
         p.guess > 2 || p.k < 1 || p.k > MAX_K || !(p.decay > 0) || p.decay > 1 || p.n_init_solves < 0 ||
-        (p.precision != SW_PRECISION_FP64 && p.precision != SW_PRECISION_MIXED)) {
-        set_error("params: restart 1..32, k 1..16, decay in (0,1], tol > 0, known guess/precision");
+        (p.precision != SW_PRECISION_FP64 && p.precision != SW_PRECISION_MIXED) || p.executor < 0 ||
+        p.executor > 2) {
+        set_error("params: restart 1..32, k 1..16, decay in (0,1], tol > 0, known guess/precision/executor");
         return SW_ERR_BAD_ARG;
     }
     Host H;
@@ -671,9 +672,14 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     return SW_OK;
 }
 
+namespace sw {
+void destroy_streamed(Problem *P);   // streamed.cu
+}
+
 extern "C" int sw_destroy_problem(sw_problem *pp) {
     Problem *P = (Problem *)pp;
     if (!P) return SW_OK;
+    destroy_streamed(P);
     for (auto ev : P->ev) cudaEventDestroy(ev);
     for (void *a : P->allocs) cudaFree(a);
     delete P;

@@ -123,7 +123,17 @@ static size_t solve_smem(const Dev &D, const Tiling &t) {
 
 static bool mixed(const Problem *P) { return P->params.precision == SW_PRECISION_MIXED; }
 
+int setup_streamed(Problem *P);                                   // streamed.cu
+int solve_streamed(Problem *P, const SolveArgs &A, cudaStream_t s);  // streamed.cu
+
 int setup_solver_launch(Problem *P) {
+    int ex = P->params.executor;
+    if (ex == SW_EXEC_AUTO) ex = P->m >= SW_EXEC_STREAMED_MIN ? SW_EXEC_STREAMED : SW_EXEC_PERSISTENT;
+    P->exec = ex;
+    if (ex == SW_EXEC_STREAMED) {
+        int rc = setup_streamed(P);
+        if (rc != SW_OK) return rc;
+    }
     Tiling t = make_tiling(P->dev);
     size_t smem = solve_smem(P->dev, t);
     const void *kern = solve_kernel_for(mixed(P), P->dev.walls != 0);
@@ -214,10 +224,15 @@ static int launch_solve(Problem *P, const double *ep, const double *ec, const do
         e = cudaEventRecord(P->ev[2 * evi], s);
         if (e != cudaSuccess) return cuda_fail(e, "event record");
     }
-    const void *kern = solve_kernel_for(mixed(P), P->dev.walls != 0);
-    e = cudaLaunchCooperativeKernel(kern, P->nblocks, NTHREADS, args, P->smem, s);
-    if (e != cudaSuccess) return cuda_fail(e, "solve launch");
-    P->launches++;
+    if (P->exec == SW_EXEC_STREAMED) {
+        int rc = solve_streamed(P, A, s);
+        if (rc != SW_OK) return rc;
+    } else {
+        const void *kern = solve_kernel_for(mixed(P), P->dev.walls != 0);
+        e = cudaLaunchCooperativeKernel(kern, P->nblocks, NTHREADS, args, P->smem, s);
+        if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+        P->launches++;
+    }
     if (evi >= 0) {
         e = cudaEventRecord(P->ev[2 * evi + 1], s);
         if (e != cudaSuccess) return cuda_fail(e, "event record");

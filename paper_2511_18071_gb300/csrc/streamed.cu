@@ -1,0 +1,797 @@
+// The Poisson solve of one stage for large problems, as a sequence of
+// high-occupancy kernels (the streamed executor).
+//
+// Same algorithm, in the same order, as the persistent solve kernel
+// (sw_solve.cuh): reference norms, the EWMA guess of Algorithms 2 and 4
+// (sketch update, W = A Y in FP64, Gram, CholeskyQR2 with the shifted
+// fallback and the rank guard, x0 = Y z), then restarted GMRES
+// left-preconditioned with the fixed ILU(0) factors (Sec. 3) with CGS2,
+// Givens rotations and the FP64 restart residual.  The difference is the
+// execution: a persistent kernel has one block per SM (8 warps), too few to
+// keep enough loads in flight when the factors, the Krylov basis and the
+// sketch live in HBM; here every bandwidth-bound phase is its own kernel with
+// as many blocks as the data needs, and the small dense steps (Hessenberg
+// column, Givens, Cholesky, stop tests) run in one-block control kernels that
+// keep their state in device memory.  Kernels of an Arnoldi step return at
+// once when the control state says the cycle or the solve has ended, so the
+// host enqueues a whole restart cycle and synchronises once per cycle.
+#include <cmath>
+#include <cstring>
+
+#include "sw_solve.cuh"
+
+namespace sw {
+
+constexpr int SNB = 4 * 152;   // blocks of the streaming reduction kernels
+
+// Control state of one streamed solve (device memory).
+struct SState {
+    double H[(MAX_RESTART + 1) * MAX_RESTART];
+    double cs[MAX_RESTART], sn[MAX_RESTART], g[MAX_RESTART + 1], y[MAX_RESTART];
+    double scale[MAX_RESTART + 1];
+    double hs[MAX_RESTART];
+    float hs32[MAX_RESTART];
+    double G[MAX_K * MAX_K], R1[MAX_K * MAX_K], R2[MAX_K * MAX_K], R[MAX_K * MAX_K];
+    double c1[MAX_K], c2[MAX_K], z[MAX_K], tmp[MAX_K];
+    double res[PART_STRIDE];
+    double braw, bnorm, res0, res_last, guess_res, inner_stop, mf, mb;
+    int iters, restarts, converged, status, stop, done, jend, guess_rank, shifted, chol_ok;
+};
+
+// ---- reductions ----------------------------------------------------------
+
+// One block: out[i] = sum over b < nb of part[i * nb + b], i < n (fixed order).
+__device__ inline void reduce_parts(const double *part, int n, int nb, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < n; i += NWARPS) {
+        double s = 0.0;
+        for (int b = lane; b < nb; b += 32) s += part[(size_t)i * nb + b];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[i] = s;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void zero32(double (&v)[32]) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = 0.0;
+}
+
+// ---- operator kernels ------------------------------------------------------
+
+__global__ void __launch_bounds__(NTHREADS) sk_geometry(Dev D, const double *ep, const double *ec) {
+    geometry_columns(D, ep, ec, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+template <typename TI, int WM>
+__global__ void __launch_bounds__(NTHREADS) sk_apply_vj(Dev D, Tiling tl, const TI *V, int j, const SState *ss,
+                                                          TI *t) {
+    if (ss->stop || ss->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TI *sp = reinterpret_cast<TI *>(smem_raw);
+    TI *sq = sp + (size_t)D.P * tl.HW;
+    LdVec<TI, TI> ld{V + (size_t)j * D.m, TI(ss->scale[j])};
+    StVec<TI, TI> st{t};
+    for (int tile = blockIdx.x; tile < tl.ntiles; tile += gridDim.x) apply_tile<TI, WM>(D, tl, tile, sp, sq, ld, st);
+}
+
+// r = b - A x with per-block partial sums of r^2 in part[blockIdx.x]
+template <int WM>
+__global__ void __launch_bounds__(NTHREADS) sk_apply_resid(Dev D, Tiling tl, const double *x, const double *b,
+                                                             double *r, double *part, const SState *ss,
+                                                             int skip_when_done) {
+    if (skip_when_done && ss->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[NWARPS * 32];
+    double *sp = reinterpret_cast<double *>(smem_raw);
+    double *sq = sp + (size_t)D.P * tl.HW;
+    StResid st{b, r, 0.0};
+    LdVec<double, double> ld{x, 1.0};
+    for (int tile = blockIdx.x; tile < tl.ntiles; tile += gridDim.x) apply_tile<double, WM>(D, tl, tile, sp, sq, ld, st);
+    double v[32];
+    zero32(v);
+    v[0] = st.acc;
+    block_partials32(v, 1, red, part, gridDim.x);
+}
+
+// W_c = A (r Y_c + omega_c x_prev) or A Y_c, FP64
+template <int WM>
+__global__ void __launch_bounds__(NTHREADS) sk_apply_w(Dev D, Tiling tl, const double *Yc, const double *xprev,
+                                                         double decay, double om, int upd, double *Wc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *sp = reinterpret_cast<double *>(smem_raw);
+    double *sq = sp + (size_t)D.P * tl.HW;
+    StVec<double, double> st{Wc};
+    if (upd) {
+        LdEwma<double, double> ld{Yc, xprev, decay, om};
+        for (int tile = blockIdx.x; tile < tl.ntiles; tile += gridDim.x) apply_tile<double, WM>(D, tl, tile, sp, sq, ld, st);
+    } else {
+        LdVec<double, double> ld{Yc, 1.0};
+        for (int tile = blockIdx.x; tile < tl.ntiles; tile += gridDim.x) apply_tile<double, WM>(D, tl, tile, sp, sq, ld, st);
+    }
+}
+
+// ---- preconditioner kernels (one column group per launch) ----------------
+
+template <typename TI, typename TIn, bool LOWER, int WM>
+__global__ void __launch_bounds__(NTHREADS) sk_ilu_gather(Dev D, int c, const TIn *in, TI *out, const SState *ss,
+                                                            int skip) {
+    if (skip && (ss->stop || ss->done)) return;
+    const long long rows = (long long)group_size<WM>(D, c) * D.P;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x)
+        ilu_gather_row<TI, TIn, LOWER, WM>(D, c, r, in, out);
+}
+
+template <typename TI, int WM>
+__global__ void __launch_bounds__(NTHREADS) sk_ilu_product(Dev D, int c, TI *out, int upper, const SState *ss,
+                                                             int skip) {
+    if (skip && (ss->stop || ss->done)) return;
+    const int lane = threadIdx.x & 31;
+    const int per = group_size<WM>(D, c);
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < per; q += nw)
+        ilu_column_product<TI, WM>(D, c, q, out, lane, upper != 0);
+}
+
+// ---- streaming vector kernels --------------------------------------------
+
+template <typename TI>
+__global__ void __launch_bounds__(NTHREADS) sk_norms_b(const double *b, const TI *t, long long m, double *part) {
+    __shared__ double red[NWARPS * 32];
+    double v[32];
+    zero32(v);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x) {
+        const double bb = b[p], tt = (double)t[p];
+        v[0] += bb * bb;
+        v[1] += tt * tt;
+    }
+    block_partials32(v, 2, red, part, gridDim.x);
+}
+
+__global__ void __launch_bounds__(NTHREADS) sk_ynew(const double *Yc, const double *xprev, double decay, double om,
+                                                     double *Ync, long long m) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x)
+        Ync[p] = decay * Yc[p] + om * xprev[p];
+}
+
+// Gram entries of W (first pass) or of Q1 = W R1^-1 (second pass), and W^T b / Q1^T b, in
+// chunks of 32 values: part[(c0 + i) * nb + block]
+__global__ void __launch_bounds__(NTHREADS) sk_gram(const double *Wm, const double *b, long long m, int k,
+                                                     const SState *ss, int second, double *part) {
+    __shared__ double red[NWARPS * 32];
+    __shared__ unsigned char ga[PART_STRIDE], gb[PART_STRIDE];
+    __shared__ double R1[MAX_K * MAX_K];
+    if (second && !ss->chol_ok) return;
+    if (threadIdx.x == 0) {
+        int e = 0;
+        for (int a = 0; a < k; ++a)
+            for (int bb = a; bb < k; ++bb, ++e) { ga[e] = (unsigned char)a; gb[e] = (unsigned char)bb; }
+    }
+    for (int i = threadIdx.x; i < k * k; i += blockDim.x) R1[i] = ss->R1[i];
+    __syncthreads();
+    const int ng = k * (k + 1) / 2, nv = ng + k;
+    for (int c0 = 0; c0 < nv; c0 += 32) {
+        double v[32];
+        zero32(v);
+        for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m;
+             p += (long long)gridDim.x * blockDim.x) {
+            double q[MAX_K];
+#pragma unroll
+            for (int c = 0; c < MAX_K; ++c) {
+                if (c >= k) { q[c] = 0.0; continue; }
+                double s = Wm[(size_t)c * m + p];
+                if (second) {
+                    for (int i = 0; i < c; ++i) s -= q[i] * R1[i * k + c];
+                    s = s / R1[c * k + c];
+                }
+                q[c] = s;
+            }
+            const double bp = b[p];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int e = c0 + i;
+                if (e >= nv) break;
+                v[i] += e < ng ? q[ga[e]] * q[gb[e]] : q[e - ng] * bp;
+            }
+        }
+        block_partials32(v, min(32, nv - c0), red, part + (size_t)c0 * gridDim.x, gridDim.x);
+    }
+}
+
+// x0 = Y z (EWMA), x_prev (previous solution) or 0 (cold start)
+__global__ void __launch_bounds__(NTHREADS) sk_x0(const double *Y, const double *xprev, const SState *ss, int k,
+                                                   int mode, double *x, long long m) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        if (mode == SW_GUESS_EWMA) {
+            for (int c = 0; c < k; ++c) s += Y[(size_t)c * m + p] * ss->z[c];
+        } else if (mode == SW_GUESS_PREVIOUS) {
+            s = xprev[p];
+        }
+        x[p] = s;
+    }
+}
+
+// ||V_0||^2 after the preconditioner: part[blockIdx.x]
+template <typename TI>
+__global__ void __launch_bounds__(NTHREADS) sk_norm(const TI *v0, long long m, double *part, const SState *ss) {
+    __shared__ double red[NWARPS * 32];
+    if (ss->done) return;
+    double v[32];
+    zero32(v);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x) {
+        const double a = (double)v0[p];
+        v[0] += a * a;
+    }
+    block_partials32(v, 1, red, part, gridDim.x);
+}
+
+// CGS2 pass 1 (d_i = V_i . w), pass 2 (w -= V h; d'_i = V_i . w) and pass 3
+// (w -= V h'; ||w||^2), as in the persistent kernel: FP32 inner vectors use
+// compensated products, the coefficient sums are FP64
+template <typename TI, int PASS>
+__global__ void __launch_bounds__(NTHREADS) sk_cgs(const TI *V, int j, TI *w, long long m, const SState *ss,
+                                                    double *part) {
+    __shared__ double red[NWARPS * 32];
+    __shared__ double hs[MAX_RESTART];
+    __shared__ float hs32[MAX_RESTART];
+    if (ss->stop || ss->done) return;
+    if (threadIdx.x < MAX_RESTART) {
+        hs[threadIdx.x] = ss->hs[threadIdx.x];
+        hs32[threadIdx.x] = ss->hs32[threadIdx.x];
+    }
+    __syncthreads();
+    double v[32];
+    zero32(v);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if constexpr (sizeof(TI) == 4) {
+        Dot2f acc[PASS == 3 ? 1 : 32];
+        for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += stride) {
+            float vb[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (float)V[(size_t)i * m + p] : 0.f;
+            float wv = (float)w[p];
+            if (PASS > 1) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    if (i > j) break;
+                    wv = fmaf(-hs32[i], vb[i], wv);
+                }
+                w[p] = TI(wv);
+            }
+            if (PASS == 3) {
+                acc[0].add(wv, wv);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    if (i > j) break;
+                    acc[i].add(vb[i], wv);
+                }
+            }
+        }
+        if (PASS == 3) {
+            v[0] = acc[0].value();
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (i > j) break;
+                v[i] = acc[i].value();
+            }
+        }
+    } else {
+        for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += stride) {
+            double vb[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (double)V[(size_t)i * m + p] : 0.0;
+            double wv = (double)w[p];
+            if (PASS > 1) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    if (i > j) break;
+                    wv -= hs[i] * vb[i];
+                }
+                w[p] = TI(wv);
+            }
+            if (PASS == 3) {
+                v[0] += wv * wv;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    if (i > j) break;
+                    v[i] += vb[i] * wv;
+                }
+            }
+        }
+    }
+    block_partials32(v, PASS == 3 ? 1 : j + 1, red, part, gridDim.x);
+}
+
+// x += V y (y already carries the basis scales), FP64
+template <typename TI>
+__global__ void __launch_bounds__(NTHREADS) sk_update_x(double *x, const TI *V, long long m, const SState *ss) {
+    __shared__ double y[MAX_RESTART];
+    __shared__ int jend;
+    if (threadIdx.x == 0) jend = ss->jend;
+    if (threadIdx.x < MAX_RESTART) y[threadIdx.x] = ss->y[threadIdx.x];
+    __syncthreads();
+    if (jend == 0) return;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x) {
+        double s = x[p];
+        for (int i = 0; i < jend; ++i) s += y[i] * (double)V[(size_t)i * m + p];
+        x[p] = s;
+    }
+}
+
+__global__ void __launch_bounds__(NTHREADS) sk_final_x(double *x, double *xprev, long long m, const SState *ss) {
+    const bool zero = ss->bnorm == 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x) {
+        if (zero) x[p] = 0.0;
+        xprev[p] = x[p];
+    }
+}
+
+// ---- one-block control kernels -------------------------------------------
+
+struct CtlArgs {
+    double tol, inner_rtol, md;
+    int k, mr, max_restarts, guess_mode;
+    CostModel cm;
+    int isz;   // bytes of an inner-precision value
+};
+
+__device__ __forceinline__ void add_cost(SState *ss, const CtlArgs &c, double f, double b) {
+    ss->mf += f * c.md;
+    ss->mb += b * c.md;
+}
+
+__global__ void sk_ctl_bnorm(const double *part, int nb, SState *ss, CtlArgs c) {
+    __shared__ double out[2];
+    reduce_parts(part, 2, nb, out);
+    if (threadIdx.x == 0) {
+        ss->braw = sqrt(out[0]);
+        ss->bnorm = sqrt(out[1]);
+        ss->iters = 0;
+        ss->restarts = 0;
+        ss->converged = 0;
+        ss->status = SW_ERR_NOT_CONVERGED;
+        ss->stop = 1;
+        ss->done = 0;
+        ss->jend = 0;
+        ss->guess_rank = -1;
+        ss->shifted = 0;
+        ss->chol_ok = 0;
+        ss->res0 = ss->res_last = ss->guess_res = 0.0;
+        ss->mf = 0.0;
+        ss->mb = 0.0;
+        add_cost(ss, c, c.cm.fM + 4.0, c.cm.bM + 8.0);
+        for (int i = 0; i < MAX_K; ++i) ss->z[i] = 0.0;
+        if (ss->bnorm == 0.0) {   // b = 0: x = 0 (written at the end), no iterations
+            ss->converged = 1;
+            ss->status = SW_OK;
+            ss->done = 1;
+        }
+    }
+}
+
+// a9, step 1: G = W^T W, c1 = W^T b, Cholesky (shifted when not numerically SPD)
+__global__ void sk_ctl_chol1(const double *part, int nb, SState *ss, CtlArgs c, long long m, int upd) {
+    __shared__ double res[PART_STRIDE];
+    const int k = c.k, ng = k * (k + 1) / 2, nv = ng + k;
+    reduce_parts(part, nv, nb, res);
+    if (threadIdx.x == 0) {
+        if (upd) add_cost(ss, c, 3.0 * k, (2.0 * k + 1.0) * 8.0);
+        add_cost(ss, c, k * c.cm.fA, k * (c.cm.bA + 8.0));
+        add_cost(ss, c, 2.0 * nv, (k + 1.0) * 8.0);
+    }
+    if (threadIdx.x < 32) {
+        int e = 0;
+        for (int a = 0; a < k; ++a)
+            for (int b = a; b < k; ++b, ++e)
+                if ((e & 31) == (int)threadIdx.x) {
+                    ss->G[a * k + b] = res[e];
+                    ss->G[b * k + a] = res[e];
+                }
+        for (int i = threadIdx.x; i < k; i += 32) ss->c1[i] = res[ng + i];
+        __syncwarp();
+        double tr = 0.0;
+        for (int i = 0; i < k; ++i) tr += ss->G[i * k + i];
+        for (int i = threadIdx.x; i < k * k; i += 32) ss->R[i] = ss->G[i];
+        __syncwarp();
+        bool ok = tr > 0.0 && warp_cholesky(ss->G, ss->R1, k);
+        int shifted = 0;
+        if (!ok && tr > 0.0) {
+            double sh = 11.0 * ((double)m * k + (double)k * (k + 1)) * 1.1102230246251565e-16 * tr;
+            for (int i = threadIdx.x; i < k * k; i += 32) ss->G[i] = ss->R[i] + ((i / k == i % k) ? sh : 0.0);
+            __syncwarp();
+            ok = warp_cholesky(ss->G, ss->R1, k);
+            shifted = 1;
+        }
+        if (threadIdx.x == 0) {
+            ss->chol_ok = ok ? 1 : 0;
+            ss->shifted = shifted;
+            if (!ok) ss->guess_rank = 0;
+        }
+    }
+}
+
+// a9, step 2: G2 = Q1^T Q1, c2 = Q1^T b; R = R2 R1 (or R1 if G2 is not SPD); z with the rank guard
+__global__ void sk_ctl_chol2(const double *part, int nb, SState *ss, CtlArgs c) {
+    __shared__ double res[PART_STRIDE];
+    if (!ss->chol_ok) return;
+    const int k = c.k, ng = k * (k + 1) / 2, nv = ng + k;
+    reduce_parts(part, nv, nb, res);
+    if (threadIdx.x == 0) add_cost(ss, c, (double)k * k + 2.0 * nv, (k + 1.0) * 8.0);
+    if (threadIdx.x < 32) {
+        int e = 0;
+        for (int a = 0; a < k; ++a)
+            for (int b = a; b < k; ++b, ++e)
+                if ((e & 31) == (int)threadIdx.x) {
+                    ss->G[a * k + b] = res[e];
+                    ss->G[b * k + a] = res[e];
+                }
+        for (int i = threadIdx.x; i < k; i += 32) ss->c2[i] = res[ng + i];
+        __syncwarp();
+        bool ok2 = warp_cholesky(ss->G, ss->R2, k);
+        if (!ok2) {
+            for (int i = threadIdx.x; i < k * k; i += 32) ss->R[i] = ss->R1[i];
+            __syncwarp();
+            warp_fwdsub_t(ss->R1, ss->c1, ss->tmp, k);
+        } else {
+            for (int e2 = threadIdx.x; e2 < k * k; e2 += 32) {
+                int a = e2 / k, bc = e2 % k;
+                double s = 0.0;
+                for (int l = a; l <= bc; ++l) s += ss->R2[a * k + l] * ss->R1[l * k + bc];
+                ss->R[e2] = bc >= a ? s : 0.0;
+            }
+            __syncwarp();
+            warp_fwdsub_t(ss->R2, ss->c2, ss->tmp, k);
+        }
+        double tiny = 1e-12 * fabs(ss->R[0]);
+        warp_backsub(ss->R, ss->tmp, ss->z, k, tiny);
+        if (threadIdx.x == 0) {
+            int rk = 0;
+            for (int j = 0; j < k; ++j) rk += fabs(ss->R[j * k + j]) > tiny;
+            ss->guess_rank = rk;
+        }
+    }
+}
+
+__global__ void sk_ctl_guess_cost(SState *ss, CtlArgs c, int upd) {
+    if (threadIdx.x != 0) return;
+    if (c.guess_mode == SW_GUESS_EWMA) {
+        add_cost(ss, c, 2.0 * c.k, c.k * 8.0 + 8.0);
+    } else {
+        if (upd) add_cost(ss, c, 3.0 * c.k, (2.0 * c.k + 1.0) * 8.0);
+        if (c.guess_mode == SW_GUESS_PREVIOUS) add_cost(ss, c, 0.0, 16.0);
+    }
+}
+
+// Start of a restart cycle: beta = ||M^-1 (b - A x)||, stop tests, reset of the Arnoldi state
+__global__ void sk_ctl_cycle(const double *partA, int nbA, const double *partB, int nbB, SState *ss, CtlArgs c,
+                             int cycle) {
+    __shared__ double r2[1], b2[1];
+    if (ss->done) return;
+    reduce_parts(partA, 1, nbA, r2);
+    reduce_parts(partB, 1, nbB, b2);
+    if (threadIdx.x != 0) return;
+    const double beta = sqrt(b2[0]);
+    add_cost(ss, c, c.cm.fA + c.cm.fM + 4.0, c.cm.bA + c.cm.bM + 8.0);
+    if (cycle == 0) {
+        ss->res0 = beta / ss->bnorm;
+        ss->guess_res = ss->braw > 0.0 ? sqrt(r2[0]) / ss->braw : sqrt(r2[0]);
+    }
+    ss->res_last = beta / ss->bnorm;
+    ss->stop = 1;
+    ss->jend = 0;
+    if (!isfinite(beta)) { ss->status = SW_ERR_NAN; ss->done = 1; return; }
+    if (beta <= c.tol * ss->bnorm) { ss->converged = 1; ss->status = SW_OK; ss->done = 1; return; }
+    if (cycle == c.max_restarts + 1) { ss->done = 1; return; }
+    if (cycle > 0) ss->restarts++;
+    ss->inner_stop = fmax(c.tol * ss->bnorm, c.inner_rtol * beta);
+    ss->scale[0] = 1.0 / beta;
+    for (int i = 0; i <= c.mr; ++i) ss->g[i] = 0.0;
+    ss->g[0] = beta;
+    ss->stop = 0;
+}
+
+// Hessenberg column from pass 1 (PASS 1) or its correction from pass 2 (PASS 2)
+template <int PASS>
+__global__ void sk_ctl_h(const double *part, int nb, int j, SState *ss) {
+    __shared__ double res[MAX_RESTART];
+    if (ss->stop || ss->done) return;
+    reduce_parts(part, j + 1, nb, res);
+    if (threadIdx.x < MAX_RESTART) {
+        const int i = threadIdx.x;
+        const double hi = i <= j ? res[i] * ss->scale[i] : 0.0;
+        if (i <= j) {
+            if (PASS == 1) ss->H[i * MAX_RESTART + j] = hi;
+            else ss->H[i * MAX_RESTART + j] += hi;
+        }
+        ss->hs[i] = i <= j ? hi * ss->scale[i] : 0.0;
+        ss->hs32[i] = (float)ss->hs[i];
+    }
+}
+
+// a5: norm of the new vector, Givens rotations, residual estimate, stop test
+__global__ void sk_ctl_givens(const double *part, int nb, int j, SState *ss, CtlArgs c) {
+    __shared__ double res[1];
+    if (ss->stop || ss->done) return;
+    reduce_parts(part, 1, nb, res);
+    if (threadIdx.x != 0) return;
+    const double hn = sqrt(res[0]);
+    ss->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    double *Hc = ss->H;
+    for (int i = 0; i < j; ++i) {
+        const double a = Hc[i * MAX_RESTART + j], bb = Hc[(i + 1) * MAX_RESTART + j];
+        Hc[i * MAX_RESTART + j] = ss->cs[i] * a + ss->sn[i] * bb;
+        Hc[(i + 1) * MAX_RESTART + j] = -ss->sn[i] * a + ss->cs[i] * bb;
+    }
+    const double a = Hc[j * MAX_RESTART + j];
+    const double den = hypot(a, hn);
+    ss->cs[j] = a / den;
+    ss->sn[j] = hn / den;
+    Hc[j * MAX_RESTART + j] = den;
+    ss->g[j + 1] = -ss->sn[j] * ss->g[j];
+    ss->g[j] = ss->cs[j] * ss->g[j];
+    add_cost(ss, c, c.cm.fA + c.cm.fM + 8.0 * (j + 1) + 2.0, c.cm.bA + c.cm.bM + (3.0 * j + 8.0) * (double)c.isz);
+    ss->iters++;
+    ss->jend = j + 1;
+    if ((fabs(ss->g[j + 1]) <= ss->inner_stop) || hn == 0.0 || j + 1 == c.mr) ss->stop = 1;
+}
+
+// a6: y = R^-1 g (scaled by the basis scales) for the update x += V y
+__global__ void sk_ctl_y(SState *ss, CtlArgs c) {
+    if (ss->done || threadIdx.x >= 32) return;
+    const int jend = ss->jend;
+    const int lane = threadIdx.x;
+    double acc = lane < jend ? ss->g[lane] : 0.0;
+    for (int i = jend - 1; i >= 0; --i) {
+        const double yi = __shfl_sync(0xffffffffu, acc, i) / ss->H[i * MAX_RESTART + i];
+        if (lane == i) ss->y[i] = yi * ss->scale[i];
+        if (lane < i) acc -= ss->H[lane * MAX_RESTART + i] * yi;
+    }
+    if (lane == 0) add_cost(ss, c, 2.0 * jend, jend * (double)c.isz + 16.0);
+}
+
+__global__ void sk_ctl_final(const double *partA, int nbA, SState *ss, CtlArgs c, DevStats *stats, int guess_only) {
+    __shared__ double r2[1];
+    if (!guess_only) reduce_parts(partA, 1, nbA, r2);
+    if (threadIdx.x != 0) return;
+    DevStats &st = *stats;
+    if (guess_only) {
+        st.guess_rank = ss->guess_rank;
+        st.cholesky_shift = ss->shifted;
+        return;
+    }
+    const double true_res = ss->braw > 0.0 ? sqrt(r2[0]) / ss->braw : sqrt(r2[0]);
+    add_cost(ss, c, c.cm.fA + 3.0, c.cm.bA + 24.0);
+    if (ss->bnorm == 0.0) { ss->converged = 1; ss->status = SW_OK; }
+    st.iterations = ss->iters;
+    st.restarts = ss->restarts;
+    st.converged = ss->converged;
+    st.status = ss->status;
+    st.res0 = ss->res0;
+    st.res_final = ss->res_last;
+    st.true_res = true_res;
+    st.guess_res = ss->guess_res;
+    st.bnorm = ss->bnorm;
+    st.braw = ss->braw;
+    st.guess_rank = ss->guess_rank;
+    st.guess_mode = c.guess_mode;
+    st.cholesky_shift = ss->shifted;
+    st.total_iterations += ss->iters;
+    st.model_flops += ss->mf;
+    st.model_bytes += ss->mb;
+}
+
+// ---- host side -------------------------------------------------------------
+
+struct Streamed {
+    SState *ss = nullptr;
+    double *partA = nullptr, *partB = nullptr;   // apply-grid partials, streaming partials
+    int *h_done = nullptr;                       // pinned flag read once per cycle
+    Tiling tl{};
+    int nbA = 0;
+};
+
+static Tiling st_tiling(const Dev &D) {
+    // as for the standalone operator: at least 304 tiles, at most 64 columns wide
+    Tiling t{};
+    if (!D.three_d) {
+        int TX = 64;
+        while (TX > 4 && (D.nx % TX != 0 || D.nx / TX < 304)) TX >>= 1;
+        t.TX = TX;
+        t.TY = 1;
+    } else {
+        int TX = 16, TY = 8;
+        while ((size_t)(TX + 6) * (TY + 6) * D.P * 2 * sizeof(double) > 150 * 1024 && TX > 4) {
+            if (TX > TY) TX >>= 1; else TY >>= 1;
+        }
+        while (D.nx % TX) TX >>= 1;
+        while (D.ny % TY) TY >>= 1;
+        t.TX = TX;
+        t.TY = TY;
+    }
+    t.HX = t.TX + 2 * HALF;
+    t.HY = D.three_d ? t.TY + 2 * HALF : 1;
+    t.HW = t.HX * t.HY;
+    t.ntx = D.nx / t.TX;
+    t.nty = D.three_d ? D.ny / t.TY : 1;
+    t.ntiles = t.ntx * t.nty;
+    return t;
+}
+
+template <typename TC>
+static size_t tile_smem(const Dev &D, const Tiling &t) { return 2 * (size_t)D.P * t.HW * sizeof(TC); }
+
+template <typename TI, int WM>
+static cudaError_t set_smem_attrs(const Dev &D, const Tiling &t) {
+    cudaError_t e = cudaFuncSetAttribute(sk_apply_vj<TI, WM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tile_smem<TI>(D, t));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sk_apply_resid<WM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem<double>(D, t));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sk_apply_w<WM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem<double>(D, t));
+    return e;
+}
+
+int setup_streamed(Problem *P) {
+    Streamed *S = new (std::nothrow) Streamed();
+    if (!S) { set_error("out of host memory"); return SW_ERR_BAD_ARG; }
+    P->streamed = S;
+    const Dev &D = P->dev;
+    S->tl = st_tiling(D);
+    S->nbA = S->tl.ntiles < SNB ? S->tl.ntiles : SNB;
+    cudaError_t e = cudaMalloc((void **)&S->ss, sizeof(SState));
+    if (e == cudaSuccess) { P->allocs.push_back(S->ss); e = cudaMemset(S->ss, 0, sizeof(SState)); }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S->partA, (size_t)S->nbA * 2 * sizeof(double));
+    if (e == cudaSuccess) P->allocs.push_back(S->partA);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S->partB, (size_t)SNB * PART_STRIDE * sizeof(double));
+    if (e == cudaSuccess) P->allocs.push_back(S->partB);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_done, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "streamed executor set-up");
+    if (D.walls) {
+        e = set_smem_attrs<double, 1>(D, S->tl);
+        if (e == cudaSuccess) e = set_smem_attrs<float, 1>(D, S->tl);
+    } else {
+        e = set_smem_attrs<double, 0>(D, S->tl);
+        if (e == cudaSuccess) e = set_smem_attrs<float, 0>(D, S->tl);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "streamed kernel attributes");
+    return SW_OK;
+}
+
+void destroy_streamed(Problem *P) {
+    Streamed *S = (Streamed *)P->streamed;
+    if (!S) return;
+    if (S->h_done) cudaFreeHost(S->h_done);
+    delete S;
+    P->streamed = nullptr;
+}
+
+// ILU application out = U^-1 L^-1 in (row-parallel gathers, per-column products)
+template <typename TI, typename TIn, int WM>
+static void st_ilu(const Problem *P, const TIn *in, TI *out, const SState *ss, int skip, cudaStream_t s) {
+    const Dev &D = P->dev;
+    const int ng = D.ngroups;
+    for (int c = 0; c < ng; ++c) {
+        const int per = P->goff_h[c + 1] - P->goff_h[c];
+        const long long rows = (long long)per * D.P;
+        const int gb = (int)((rows + NTHREADS - 1) / NTHREADS);
+        const int pb = (per * 32 + NTHREADS - 1) / NTHREADS;
+        sk_ilu_gather<TI, TIn, true, WM><<<gb, NTHREADS, 0, s>>>(D, c, in, out, ss, skip);
+        sk_ilu_product<TI, WM><<<pb, NTHREADS, 0, s>>>(D, c, out, 0, ss, skip);
+    }
+    for (int c = ng - 1; c >= 0; --c) {
+        const int per = P->goff_h[c + 1] - P->goff_h[c];
+        const long long rows = (long long)per * D.P;
+        const int gb = (int)((rows + NTHREADS - 1) / NTHREADS);
+        const int pb = (per * 32 + NTHREADS - 1) / NTHREADS;
+        if (c < ng - 1) sk_ilu_gather<TI, TI, false, WM><<<gb, NTHREADS, 0, s>>>(D, c, out, out, ss, skip);
+        sk_ilu_product<TI, WM><<<pb, NTHREADS, 0, s>>>(D, c, out, 1, ss, skip);
+    }
+}
+
+template <typename TI, int WM>
+static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
+    Streamed *S = (Streamed *)P->streamed;
+    const Dev &D = P->dev;
+    const long long m = D.m;
+    const Tiling &tl = S->tl;
+    const size_t smI = tile_smem<TI>(D, tl), smD = tile_smem<double>(D, tl);
+    SState *ss = S->ss;
+    TI *V = reinterpret_cast<TI *>(A.V);
+    TI *tw = reinterpret_cast<TI *>(A.t);
+    const int k = A.k, mr = A.restart;
+    CtlArgs c{A.tol, A.inner_rtol, (double)m, k, mr, A.max_restarts, A.guess_mode, A.cm, (int)sizeof(TI)};
+    const int gc = (D.ncol + NTHREADS - 1) / NTHREADS;
+    long long launches = 0;
+    // a1: geometry of the stage pair
+    sk_geometry<<<gc, NTHREADS, 0, s>>>(D, A.eta_prev, A.eta_cur);
+    // reference norms ||b|| and ||M^-1 b||
+    st_ilu<TI, double, WM>(P, A.b, tw, ss, 0, s);
+    sk_norms_b<TI><<<SNB, NTHREADS, 0, s>>>(A.b, tw, m, S->partB);
+    sk_ctl_bnorm<<<1, NTHREADS, 0, s>>>(S->partB, SNB, ss, c);
+    launches += 3 + 4 * D.ngroups;
+    // a7-a10: guess
+    const int upd = A.pending;
+    if (upd || A.guess_mode == SW_GUESS_EWMA) {
+        for (int cc = 0; cc < k; ++cc) {
+            const double *Yc = A.Yold + (size_t)cc * m;
+            double *Ync = A.Ynew + (size_t)cc * m;
+            if (upd) { sk_ynew<<<SNB, NTHREADS, 0, s>>>(Yc, A.xprev, A.decay, A.omega[cc], Ync, m); ++launches; }
+            if (A.guess_mode == SW_GUESS_EWMA) {
+                sk_apply_w<WM><<<tl.ntiles, NTHREADS, smD, s>>>(D, tl, Yc, A.xprev, A.decay, A.omega[cc], upd,
+                                                                 A.Wm + (size_t)cc * m);
+                ++launches;
+            }
+        }
+    }
+    const double *Ycur = A.pending ? A.Ynew : A.Yold;
+    if (A.guess_mode == SW_GUESS_EWMA) {
+        sk_gram<<<SNB, NTHREADS, 0, s>>>(A.Wm, A.b, m, k, ss, 0, S->partB);
+        sk_ctl_chol1<<<1, NTHREADS, 0, s>>>(S->partB, SNB, ss, c, m, upd);
+        sk_gram<<<SNB, NTHREADS, 0, s>>>(A.Wm, A.b, m, k, ss, 1, S->partB);
+        sk_ctl_chol2<<<1, NTHREADS, 0, s>>>(S->partB, SNB, ss, c);
+        launches += 4;
+    }
+    sk_x0<<<SNB, NTHREADS, 0, s>>>(Ycur, A.xprev, ss, k, A.guess_mode, A.x, m);
+    sk_ctl_guess_cost<<<1, 32, 0, s>>>(ss, c, upd);
+    launches += 2;
+    if (A.guess_only) {
+        sk_ctl_final<<<1, NTHREADS, 0, s>>>(S->partA, S->nbA, ss, c, A.stats, 1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "streamed guess launch");
+        P->launches += launches + 1;
+        return SW_OK;
+    }
+    // restarted GMRES: one host synchronisation per cycle
+    for (int cycle = 0; cycle <= A.max_restarts + 1; ++cycle) {
+        sk_apply_resid<WM><<<S->nbA, NTHREADS, smD, s>>>(D, tl, A.x, A.b, A.r, S->partA, ss, 1);
+        st_ilu<TI, double, WM>(P, A.r, V, ss, 0, s);
+        sk_norm<TI><<<SNB, NTHREADS, 0, s>>>(V, m, S->partB, ss);
+        sk_ctl_cycle<<<1, NTHREADS, 0, s>>>(S->partA, S->nbA, S->partB, SNB, ss, c, cycle);
+        cudaError_t e = cudaMemcpyAsync(S->h_done, &ss->done, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "streamed cycle");
+        launches += 3 + 4 * D.ngroups;
+        if (*S->h_done) break;
+        for (int j = 0; j < mr; ++j) {
+            TI *w = V + (size_t)(j + 1) * m;
+            sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, j, ss, tw);
+            st_ilu<TI, TI, WM>(P, tw, w, ss, 1, s);
+            sk_cgs<TI, 1><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, S->partB);
+            sk_ctl_h<1><<<1, NTHREADS, 0, s>>>(S->partB, SNB, j, ss);
+            sk_cgs<TI, 2><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, S->partB);
+            sk_ctl_h<2><<<1, NTHREADS, 0, s>>>(S->partB, SNB, j, ss);
+            sk_cgs<TI, 3><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, S->partB);
+            sk_ctl_givens<<<1, NTHREADS, 0, s>>>(S->partB, SNB, j, ss, c);
+            launches += 7 + 4 * D.ngroups;
+        }
+        sk_ctl_y<<<1, 32, 0, s>>>(ss, c);
+        sk_update_x<TI><<<SNB, NTHREADS, 0, s>>>(A.x, V, m, ss);
+        launches += 2;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "streamed cycle launch");
+    }
+    // true residual ||b - A x|| / ||b|| in FP64; the solution is kept for the next guess
+    sk_final_x<<<SNB, NTHREADS, 0, s>>>(A.x, A.xprev, m, ss);
+    sk_apply_resid<WM><<<S->nbA, NTHREADS, smD, s>>>(D, tl, A.x, A.b, A.r, S->partA, ss, 0);
+    sk_ctl_final<<<1, NTHREADS, 0, s>>>(S->partA, S->nbA, ss, c, A.stats, 0);
+    launches += 3;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "streamed final launch");
+    P->launches += launches;
+    return SW_OK;
+}
+
+int solve_streamed(Problem *P, const SolveArgs &A, cudaStream_t s) {
+    const bool f32 = P->params.precision == SW_PRECISION_MIXED;
+    if (P->dev.walls) return f32 ? st_solve<float, 1>(P, A, s) : st_solve<double, 1>(P, A, s);
+    return f32 ? st_solve<float, 0>(P, A, s) : st_solve<double, 0>(P, A, s);
+}
+
+}  // namespace sw

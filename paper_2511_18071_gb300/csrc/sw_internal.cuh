@@ -132,6 +132,8 @@ struct Problem {
     long long total_iterations = 0;
     int stage = 0;                 // next Runge-Kutta stage, 0..4
     int nblocks = 0, nthreads = 0;
+    int exec = SW_EXEC_PERSISTENT;  // resolved executor of the solves
+    void *streamed = nullptr;      // state of the streamed executor
     size_t smem = 0;
     cudaStream_t last_stream = nullptr;
     bool has_state = false;

@@ -48,10 +48,11 @@ def _surfaces(nx, ny, seed):
 
 
 @pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
-def test_mixed_refined_solution_matches_fp64_oracle(sw, case):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_mixed_refined_solution_matches_fp64_oracle(sw, case, executor):
     name, nx, ny, nz, lx, ly, h = case
     kw = dict(restart=20, max_restarts=400, tol=1e-12, guess="cold")
-    gpu = sw.Problem(nx, ny, nz, lx, ly, h, precision="mixed", **kw)
+    gpu = sw.Problem(nx, ny, nz, lx, ly, h, precision="mixed", executor=executor, **kw)
     ora = O.OracleProblem(nx, ny, nz, lx, ly, h, **kw)
     e1, e2 = _surfaces(nx, ny, 4)
     b = np.random.default_rng(5).standard_normal(ora.m)
@@ -65,10 +66,11 @@ def test_mixed_refined_solution_matches_fp64_oracle(sw, case):
     assert err <= 1e-10, (name, err, so["iterations"], sg["iterations"])
 
 
-def test_mixed_trajectory_meets_tolerance(sw):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_mixed_trajectory_meets_tolerance(sw, executor):
     wl = W.airy_2d()
     kw = dict(restart=20, max_restarts=100, tol=1e-8, guess="ewma", k=8, decay=0.9, n_init_solves=10)
-    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], precision="mixed", **kw)
+    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], precision="mixed", executor=executor, **kw)
     ora = O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
     st = W.state_arrays(wl)
     phys = (wl["g"], wl["rho"], wl["dt"])

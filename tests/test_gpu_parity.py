@@ -99,10 +99,11 @@ def _rhs(ora, nz, seed):
 
 
 @pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
-def test_cold_solve_tight(sw, case):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_cold_solve_tight(sw, case, executor):
     name, nx, ny, nz, lx, ly, h = case
     kw = dict(restart=20, max_restarts=300, tol=1e-12, guess="cold")
-    gpu = sw.Problem(nx, ny, nz, lx, ly, h, **kw)
+    gpu = sw.Problem(nx, ny, nz, lx, ly, h, executor=executor, **kw)
     ora = O.OracleProblem(nx, ny, nz, lx, ly, h, **kw)
     e1, e2 = _surfaces(nx, ny, 4)
     b = _rhs(ora, nz, 5)
@@ -139,11 +140,12 @@ def _record(wl, nsteps, **kw):
 
 
 @pytest.mark.parametrize("guess", ["previous", "ewma"])
-def test_trajectory_iterations_and_solutions(sw, guess):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_trajectory_iterations_and_solutions(sw, guess, executor):
     wl = W.airy_2d()
     kw = dict(restart=20, max_restarts=100, tol=1e-8, guess=guess, k=8, decay=0.9, n_init_solves=10)
     rec = _record(wl, 8, **kw)
-    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
+    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], executor=executor, **kw)
     x = torch.zeros(gpu.m, dtype=torch.float64, device=DEV)
     diffs = []
     for ep, ec, b, p, so in rec:
@@ -158,11 +160,12 @@ def test_trajectory_iterations_and_solutions(sw, guess):
     assert np.count_nonzero(diffs) <= len(diffs) // 5, diffs
 
 
-def test_sketch_after_solves_matches_oracle(sw):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_sketch_after_solves_matches_oracle(sw, executor):
     wl = W.airy_2d()
     kw = dict(restart=20, max_restarts=100, tol=1e-12, guess="ewma", k=5, decay=0.8, n_init_solves=2)
     rec = _record(wl, 1, **kw)
-    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
+    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], executor=executor, **kw)
     ora = O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
     x = torch.zeros(gpu.m, dtype=torch.float64, device=DEV)
     for ep, ec, b, p, so in rec:
@@ -176,13 +179,14 @@ def test_sketch_after_solves_matches_oracle(sw):
     assert np.abs(Yg - Yo).max() <= 1e-9 * np.abs(Yo).max()
 
 
-def test_subspace_guess_matches_oracle(sw):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_subspace_guess_matches_oracle(sw, executor):
     nx, nz, L = 64, 9, 2 * math.pi
     x64 = np.arange(nx) * (L / nx)
     h = 1.0 - 0.3 * np.exp(-3 * (x64 - 3.0) ** 2)
     k = 6
     kw = dict(k=k, guess="ewma")
-    gpu = sw.Problem(nx, 1, nz, L, 0.0, h, **kw)
+    gpu = sw.Problem(nx, 1, nz, L, 0.0, h, executor=executor, **kw)
     ora = O.OracleProblem(nx, 1, nz, L, 0.0, h, **kw)
     rng = np.random.default_rng(9)
     Y = rng.standard_normal((ora.m, k))
@@ -199,12 +203,13 @@ def test_subspace_guess_matches_oracle(sw):
     assert rank == k and err < 1e-10, err
 
 
-def test_in_span_solution_needs_no_iterations(sw):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_in_span_solution_needs_no_iterations(sw, executor):
     nx, nz, L = 64, 9, 2 * math.pi
     h = np.ones(nx)
     k = 4
     kw = dict(k=k, guess="ewma", n_init_solves=0, tol=1e-8)
-    gpu = sw.Problem(nx, 1, nz, L, 0.0, h, **kw)
+    gpu = sw.Problem(nx, 1, nz, L, 0.0, h, executor=executor, **kw)
     ora = O.OracleProblem(nx, 1, nz, L, 0.0, h, **kw)
     e1, e2 = _surfaces(nx, 1, 12)
     ora.assemble(e1, e2)
@@ -219,9 +224,10 @@ def test_in_span_solution_needs_no_iterations(sw):
     assert sg["status"] == 0 and sg["iterations"] == 0, sg
 
 
-def test_zero_rhs_and_iteration_cap(sw):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_zero_rhs_and_iteration_cap(sw, executor):
     nx, nz, L = 32, 9, 2 * math.pi
-    gpu = sw.Problem(nx, 1, nz, L, 0.0, np.ones(nx), restart=2, max_restarts=0, tol=1e-14)
+    gpu = sw.Problem(nx, 1, nz, L, 0.0, np.ones(nx), restart=2, max_restarts=0, tol=1e-14, executor=executor)
     e1, e2 = _surfaces(nx, 1, 14)
     x = torch.ones(gpu.m, dtype=torch.float64, device=DEV)
     gpu.solve(_t(e1), _t(e2), torch.zeros(gpu.m, dtype=torch.float64, device=DEV), x)
@@ -234,9 +240,10 @@ def test_zero_rhs_and_iteration_cap(sw):
     assert sg["status"] == -3 and sg["iterations"] == 2 and not sg["converged"], sg
 
 
-def test_nan_rhs_reported(sw):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_nan_rhs_reported(sw, executor):
     nx, nz, L = 32, 9, 2 * math.pi
-    gpu = sw.Problem(nx, 1, nz, L, 0.0, np.ones(nx))
+    gpu = sw.Problem(nx, 1, nz, L, 0.0, np.ones(nx), executor=executor)
     e1, e2 = _surfaces(nx, 1, 16)
     b = np.zeros(gpu.m)
     b[5] = np.nan
@@ -245,11 +252,12 @@ def test_nan_rhs_reported(sw):
     assert gpu.stats()["status"] == -5
 
 
-def test_stage_driver_matches_oracle(sw):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_stage_driver_matches_oracle(sw, executor):
     wl = W.airy_2d()
     kw = dict(restart=20, max_restarts=200, tol=1e-12, guess="previous")
     ora = O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
-    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
+    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], executor=executor, **kw)
     st = W.state_arrays(wl)
     sw.set_physics(gpu.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
     sw.set_state(gpu.handle, _t(wl["u"]), None, _t(wl["w"]), _t(wl["eta"]))

@@ -98,10 +98,11 @@ def test_walls_apply_preconditioner(sw, case):
 
 
 @pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
-def test_walls_cold_solve_tight(sw, case):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_walls_cold_solve_tight(sw, case, executor):
     name, nx, nz, lx, h = case
     kw = dict(restart=20, max_restarts=300, tol=1e-12, guess="cold")
-    gpu = sw.Problem(nx, 1, nz, lx, 0.0, h, walls=True, **kw)
+    gpu = sw.Problem(nx, 1, nz, lx, 0.0, h, walls=True, executor=executor, **kw)
     ora = O.OracleProblem(nx, 1, nz, lx, 0.0, h, walls=True, **kw)
     e1, e2 = _surfaces(nx, lx, 4)
     b = _rhs(ora, nz, 5)
@@ -115,10 +116,11 @@ def test_walls_cold_solve_tight(sw, case):
     assert abs(sg["iterations"] - so["iterations"]) <= 1, (sg, so)
 
 
-def test_walls_mixed_precision_solve(sw):
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_walls_mixed_precision_solve(sw, executor):
     name, nx, nz, lx, h = _cases()[1]
     kw = dict(restart=20, max_restarts=300, tol=1e-10, guess="cold")
-    gpu = sw.Problem(nx, 1, nz, lx, 0.0, h, walls=True, precision="mixed", **kw)
+    gpu = sw.Problem(nx, 1, nz, lx, 0.0, h, walls=True, precision="mixed", executor=executor, **kw)
     ora = O.OracleProblem(nx, 1, nz, lx, 0.0, h, walls=True, **dict(kw, tol=1e-13))
     e1, e2 = _surfaces(nx, lx, 6)
     b = _rhs(ora, nz, 7)
