@@ -44,8 +44,18 @@ struct SState {
 __device__ inline void reduce_parts(const double *part, int n, int nb, double *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = warp; i < n; i += NWARPS) {
-        double s = 0.0;
-        for (int b = lane; b < nb; b += 32) s += part[(size_t)i * nb + b];
+        // four independent accumulators keep four loads in flight per lane
+        const double *pi = part + (size_t)i * nb;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int b = lane;
+        for (; b + 96 < nb; b += 128) {
+            s0 += pi[b];
+            s1 += pi[b + 32];
+            s2 += pi[b + 64];
+            s3 += pi[b + 96];
+        }
+        for (; b < nb; b += 32) s0 += pi[b];
+        double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) out[i] = s;
@@ -229,8 +239,10 @@ __global__ void __launch_bounds__(NTHREADS) sk_norm(const TI *v0, long long m, d
 
 // CGS2 pass 1 (d_i = V_i . w), pass 2 (w -= V h; d'_i = V_i . w) and pass 3
 // (w -= V h'; ||w||^2), as in the persistent kernel: FP32 inner vectors use
-// compensated products, the coefficient sums are FP64
-template <typename TI, int PASS>
+// compensated products, the coefficient sums are FP64.  NJ >= j + 1 sizes the
+// per-thread arrays, so short Arnoldi prefixes need few registers and the
+// kernel keeps more warps resident.
+template <typename TI, int PASS, int NJ>
 __global__ void __launch_bounds__(NTHREADS) sk_cgs(const TI *V, int j, TI *w, long long m, const SState *ss,
                                                     double *part) {
     __shared__ double red[NWARPS * 32];
@@ -242,19 +254,21 @@ __global__ void __launch_bounds__(NTHREADS) sk_cgs(const TI *V, int j, TI *w, lo
         hs32[threadIdx.x] = ss->hs32[threadIdx.x];
     }
     __syncthreads();
-    double v[32];
-    zero32(v);
+    constexpr int NA = PASS == 3 ? 1 : NJ;
+    double d[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) d[i] = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     if constexpr (sizeof(TI) == 4) {
-        Dot2f acc[PASS == 3 ? 1 : 32];
+        Dot2f acc[NA];
         for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += stride) {
-            float vb[32];
+            float vb[NJ];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (float)V[(size_t)i * m + p] : 0.f;
+            for (int i = 0; i < NJ; ++i) vb[i] = i <= j ? (float)V[(size_t)i * m + p] : 0.f;
             float wv = (float)w[p];
             if (PASS > 1) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
+                for (int i = 0; i < NJ; ++i) {
                     if (i > j) break;
                     wv = fmaf(-hs32[i], vb[i], wv);
                 }
@@ -264,47 +278,52 @@ __global__ void __launch_bounds__(NTHREADS) sk_cgs(const TI *V, int j, TI *w, lo
                 acc[0].add(wv, wv);
             } else {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
+                for (int i = 0; i < NA; ++i) {
                     if (i > j) break;
                     acc[i].add(vb[i], wv);
                 }
             }
         }
-        if (PASS == 3) {
-            v[0] = acc[0].value();
-        } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                if (i > j) break;
-                v[i] = acc[i].value();
-            }
-        }
+        for (int i = 0; i < NA; ++i) d[i] = acc[i].value();
     } else {
         for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += stride) {
-            double vb[32];
+            double vb[NJ];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) vb[i] = i <= j ? (double)V[(size_t)i * m + p] : 0.0;
+            for (int i = 0; i < NJ; ++i) vb[i] = i <= j ? (double)V[(size_t)i * m + p] : 0.0;
             double wv = (double)w[p];
             if (PASS > 1) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
+                for (int i = 0; i < NJ; ++i) {
                     if (i > j) break;
                     wv -= hs[i] * vb[i];
                 }
                 w[p] = TI(wv);
             }
             if (PASS == 3) {
-                v[0] += wv * wv;
+                d[0] += wv * wv;
             } else {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
+                for (int i = 0; i < NA; ++i) {
                     if (i > j) break;
-                    v[i] += vb[i] * wv;
+                    d[i] += vb[i] * wv;
                 }
             }
         }
     }
+    double v[32];
+    zero32(v);
+#pragma unroll
+    for (int i = 0; i < NA; ++i) v[i] = d[i];
     block_partials32(v, PASS == 3 ? 1 : j + 1, red, part, gridDim.x);
+}
+
+template <typename TI, int PASS>
+static void launch_cgs(const TI *V, int j, TI *w, long long m, const SState *ss, double *part, cudaStream_t s) {
+    if (j < 4) sk_cgs<TI, PASS, 4><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
+    else if (j < 8) sk_cgs<TI, PASS, 8><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
+    else if (j < 16) sk_cgs<TI, PASS, 16><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
+    else sk_cgs<TI, PASS, 32><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
 }
 
 // x += V y (y already carries the basis scales), FP64
@@ -763,11 +782,11 @@ static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
             TI *w = V + (size_t)(j + 1) * m;
             sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, j, ss, tw);
             st_ilu<TI, TI, WM>(P, tw, w, ss, 1, s);
-            sk_cgs<TI, 1><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, S->partB);
+            launch_cgs<TI, 1>(V, j, w, m, ss, S->partB, s);
             sk_ctl_h<1><<<1, NTHREADS, 0, s>>>(S->partB, SNB, j, ss);
-            sk_cgs<TI, 2><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, S->partB);
+            launch_cgs<TI, 2>(V, j, w, m, ss, S->partB, s);
             sk_ctl_h<2><<<1, NTHREADS, 0, s>>>(S->partB, SNB, j, ss);
-            sk_cgs<TI, 3><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, S->partB);
+            launch_cgs<TI, 3>(V, j, w, m, ss, S->partB, s);
             sk_ctl_givens<<<1, NTHREADS, 0, s>>>(S->partB, SNB, j, ss, c);
             launches += 7 + 4 * D.ngroups;
         }

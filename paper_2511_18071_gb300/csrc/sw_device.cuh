@@ -487,20 +487,24 @@ __device__ __forceinline__ void column_block_product(const T *bt, const T (&g)[2
     // One level per lane.  Predicated-off FP64 instructions still take their
     // issue slots on this GPU, so the second half (levels 32..63) is not
     // issued at all here: half the multiply-adds of the general form.
+    // The block's rows are loaded eight at a time before they are used, so a
+    // warp has eight independent loads in flight instead of one.
     T a0 = T(0), a1 = T(0);
     const bool on = lane < P;
-    int a2 = 0;
-    for (; a2 + 1 < P; a2 += 2) {
-        const T g0 = __shfl_sync(0xffffffffu, g[0], a2);
-        const T g1 = __shfl_sync(0xffffffffu, g[0], a2 + 1);
-        if (on) {
-            a0 += bt[a2 * P + lane] * g0;
-            a1 += bt[(a2 + 1) * P + lane] * g1;
+    for (int a2 = 0; a2 < P; a2 += 8) {
+        T b8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) b8[u] = (on && a2 + u < P) ? bt[(a2 + u) * P + lane] : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            if (a2 + u >= P) break;
+            const T g0 = __shfl_sync(0xffffffffu, g[0], a2 + u);
+            a0 += b8[u] * g0;
+            if (a2 + u + 1 < P) {
+                const T g1 = __shfl_sync(0xffffffffu, g[0], a2 + u + 1);
+                a1 += b8[u + 1] * g1;
+            }
         }
-    }
-    if (a2 < P) {
-        const T g0 = __shfl_sync(0xffffffffu, g[0], a2);
-        if (on) a0 += bt[a2 * P + lane] * g0;
     }
     y[0] = a0 + a1;
     y[1] = T(0);
