@@ -133,6 +133,7 @@ def oracle_run(args, warm_steps, timed_steps, budget_s=None):
     import workloads as W
     wl = workload()
     kw = solver_kw(args, "ewma")
+    kw.pop("executor", None)   # how the library runs a solve; the oracle has one way
     P = O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
     st = W.state_arrays(wl)
     phys = (wl["g"], wl["rho"], wl["dt"])

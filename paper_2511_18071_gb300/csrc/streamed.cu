@@ -607,6 +607,8 @@ __global__ void sk_ctl_final(const double *partA, int nbA, SState *ss, CtlArgs c
 // ---- host side -------------------------------------------------------------
 
 struct Streamed {
+    cudaGraphExec_t cycle = nullptr;             // the Arnoldi steps of one restart cycle
+    long long cycle_kernels = 0;
     SState *ss = nullptr;
     double *partA = nullptr, *partB = nullptr;   // apply-grid partials, streaming partials
     int *h_done = nullptr;                       // pinned flag read once per cycle
@@ -687,6 +689,7 @@ void destroy_streamed(Problem *P) {
     Streamed *S = (Streamed *)P->streamed;
     if (!S) return;
     if (S->h_done) cudaFreeHost(S->h_done);
+    if (S->cycle) cudaGraphExecDestroy(S->cycle);
     delete S;
     P->streamed = nullptr;
 }
@@ -712,6 +715,56 @@ static void st_ilu(const Problem *P, const TIn *in, TI *out, const SState *ss, i
         if (c < ng - 1) sk_ilu_gather<TI, TI, false, WM><<<gb, NTHREADS, 0, s>>>(D, c, out, out, ss, skip);
         sk_ilu_product<TI, WM><<<pb, NTHREADS, 0, s>>>(D, c, out, 1, ss, skip);
     }
+}
+
+// The restart length's Arnoldi steps; every kernel reads only problem-owned
+// buffers, so the sequence is captured once per problem and replayed.
+template <typename TI, int WM>
+static long long enqueue_cycle(const Problem *P, TI *V, TI *tw, SState *ss, double *partB, const CtlArgs &c,
+                               cudaStream_t s) {
+    const Dev &D = P->dev;
+    const Streamed *S = (const Streamed *)P->streamed;
+    const Tiling &tl = S->tl;
+    const long long m = D.m;
+    const size_t smI = tile_smem<TI>(D, tl);
+    long long n = 0;
+    for (int j = 0; j < P->params.restart; ++j) {
+        TI *w = V + (size_t)(j + 1) * m;
+        sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, j, ss, tw);
+        st_ilu<TI, TI, WM>(P, tw, w, ss, 1, s);
+        launch_cgs<TI, 1>(V, j, w, m, ss, partB, s);
+        sk_ctl_h<1><<<1, NTHREADS, 0, s>>>(partB, SNB, j, ss);
+        launch_cgs<TI, 2>(V, j, w, m, ss, partB, s);
+        sk_ctl_h<2><<<1, NTHREADS, 0, s>>>(partB, SNB, j, ss);
+        launch_cgs<TI, 3>(V, j, w, m, ss, partB, s);
+        sk_ctl_givens<<<1, NTHREADS, 0, s>>>(partB, SNB, j, ss, c);
+        n += 7 + 4 * D.ngroups;
+    }
+    return n;
+}
+
+template <typename TI, int WM>
+static int build_cycle_graph(Problem *P, TI *V, TI *tw, const CtlArgs &c) {
+    Streamed *S = (Streamed *)P->streamed;
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    long long n = 0;
+    if (e == cudaSuccess) {
+        n = enqueue_cycle<TI, WM>(P, V, tw, S->ss, S->partB, c, cs);
+        e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&S->cycle, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        S->cycle = nullptr;
+        return cuda_fail(e, "restart-cycle graph");
+    }
+    S->cycle_kernels = n;
+    return SW_OK;
 }
 
 template <typename TI, int WM>
@@ -778,18 +831,20 @@ static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
         if (e != cudaSuccess) return cuda_fail(e, "streamed cycle");
         launches += 3 + 4 * D.ngroups;
         if (*S->h_done) break;
-        for (int j = 0; j < mr; ++j) {
-            TI *w = V + (size_t)(j + 1) * m;
-            sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, j, ss, tw);
-            st_ilu<TI, TI, WM>(P, tw, w, ss, 1, s);
-            launch_cgs<TI, 1>(V, j, w, m, ss, S->partB, s);
-            sk_ctl_h<1><<<1, NTHREADS, 0, s>>>(S->partB, SNB, j, ss);
-            launch_cgs<TI, 2>(V, j, w, m, ss, S->partB, s);
-            sk_ctl_h<2><<<1, NTHREADS, 0, s>>>(S->partB, SNB, j, ss);
-            launch_cgs<TI, 3>(V, j, w, m, ss, S->partB, s);
-            sk_ctl_givens<<<1, NTHREADS, 0, s>>>(S->partB, SNB, j, ss, c);
-            launches += 7 + 4 * D.ngroups;
+        // the Arnoldi steps of the cycle: one graph launch (the kernels of the
+        // steps after the stop test return at once)
+        if (!S->cycle) {
+            // the Arnoldi steps use only the per-problem fields of the control arguments
+            CtlArgs cg = c;
+            cg.guess_mode = 0;
+            cg.tol = 0.0;
+            cg.inner_rtol = 0.0;
+            int rc = build_cycle_graph<TI, WM>(P, V, tw, cg);
+            if (rc != SW_OK) return rc;
         }
+        e = cudaGraphLaunch(S->cycle, s);
+        if (e != cudaSuccess) return cuda_fail(e, "restart-cycle graph launch");
+        launches += S->cycle_kernels;
         sk_ctl_y<<<1, 32, 0, s>>>(ss, c);
         sk_update_x<TI><<<SNB, NTHREADS, 0, s>>>(A.x, V, m, ss);
         launches += 2;
