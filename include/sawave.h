@@ -233,6 +233,16 @@ int sw_destroy_batch(sw_batch *b);
  * problems were given to sw_create_batch.  Per-member results via sw_get_stats. */
 int sw_batch_solve(sw_batch *b, const double *const *d_eta_prev, const double *const *d_eta_cur,
                    const double *const *d_b, double *const *d_x, void *stream);
+/* Thread blocks per member for the batch's solves: 1 gives every member one
+ * thread block, so that up to one member per SM run at once; 2, 4,
+ * 8 or 16 give every member a thread-block cluster of that many blocks (one
+ * per SM, cluster barriers and partial sums through distributed shared
+ * memory), which shortens large members at the cost of fewer members at once.
+ * The default set by sw_create_batch is a 16-block cluster (or the largest
+ * the device can place) when the members average 4,096 unknowns or more, else
+ * one block.  SW_ERR_BAD_ARG for other values or when the device cannot place
+ * such a cluster with this batch's shared memory. */
+int sw_batch_set_cluster(sw_batch *b, int blocks_per_member);
 /* One Runge-Kutta stage of every member (each needs its state and physics set).
  * Relaxation zones set with sw_set_relaxation are not applied here. */
 int sw_batch_advance_stage(sw_batch *b, void *stream);

@@ -105,6 +105,7 @@ def lib():
         L.sw_destroy_batch.argtypes = [vp]
         L.sw_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sw_batch_advance_stage.argtypes = [vp, vp]
+        L.sw_batch_set_cluster.argtypes = [vp, ip]
         L.sw_get_solve_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
         L.sw_last_error.restype = C.c_char_p
         for name in ["sw_create_problem", "sw_destroy_problem", "sw_problem_size", "sw_solve_poisson",
@@ -112,7 +113,7 @@ def lib():
                      "sw_subspace_guess", "sw_get_sketch", "sw_set_sketch", "sw_draw_omega", "sw_set_physics",
                      "sw_set_state", "sw_get_state", "sw_advance_stage", "sw_enable_timing", "sw_get_solve_time",
                      "sw_get_last_system", "sw_apply_operator_noalloc", "sw_get_phase_times", "sw_create_batch",
-                     "sw_destroy_batch", "sw_batch_solve", "sw_batch_advance_stage", "sw_set_relaxation",
+                     "sw_destroy_batch", "sw_batch_solve", "sw_batch_advance_stage", "sw_batch_set_cluster", "sw_set_relaxation",
                      "sw_set_step"]:
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -328,6 +329,10 @@ class Batch:
 
     def solve(self, eta_prev, eta_cur, rhs, x, stream=None):
         return batch_solve(self.handle, eta_prev, eta_cur, rhs, x, stream)
+
+    def set_cluster(self, blocks_per_member):
+        """Thread blocks per member (1, or a cluster of 2, 4, 8, 16)."""
+        return _check(lib().sw_batch_set_cluster(self.handle, int(blocks_per_member)))
 
     def advance_stage(self, stream=None):
         return batch_advance_stage(self.handle, stream)

@@ -63,6 +63,7 @@ struct SmemFixed {
     double c1[MAX_K], c2[MAX_K], z[MAX_K], tmp[MAX_K];
     int flags[8];
     unsigned char ga[PART_STRIDE], gb[PART_STRIDE];   // Gram entry e -> (row, column), row <= column
+    double xchg[2 * PART_STRIDE];   // cluster team: this block's partial sums, read by the other blocks
 };
 
 // ---- teams ----
@@ -127,6 +128,59 @@ struct BlockTeam {
             fill(c0, v);
             block_partials32(v, min(32, nv - c0), S.red, out + c0, 1, true, 0);
         }
+    }
+};
+
+// A thread-block cluster owns the instance (batch members): hardware cluster
+// barriers separate the phases, and partial sums are exchanged through
+// distributed shared memory.  Every block sums the blocks' partials in rank
+// order, so all blocks hold bit-identical totals and take the same decisions.
+// Partial buffers alternate: a buffer is rewritten only after the next
+// reduction's barrier, which every reader of it has passed.
+constexpr int MAX_CLUSTER = 16;
+struct ClusterTeam {
+    cg::cluster_group cl;
+    int nb, bid;
+    double *xbuf;
+    int pbuf;
+    __device__ ClusterTeam(double *xb)
+        : cl(cg::this_cluster()), nb((int)cg::this_cluster().num_blocks()),
+          bid((int)cg::this_cluster().block_rank()), xbuf(xb), pbuf(0) {}
+    __device__ void sync() { cl.sync(); }
+    __device__ double *next_part() {
+        double *q = xbuf + pbuf * PART_STRIDE;
+        pbuf ^= 1;
+        return q;
+    }
+    // out[i] = sum over the cluster's blocks of pt[i], i < nv, in rank order
+    __device__ void cluster_sum(double *pt, int nv, double *out) {
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+            double t[MAX_CLUSTER];
+#pragma unroll
+            for (int r = 0; r < MAX_CLUSTER; ++r) t[r] = r < nb ? cl.map_shared_rank(pt, r)[i] : 0.0;
+            double s = 0.0;
+#pragma unroll
+            for (int r = 0; r < MAX_CLUSTER; ++r) s += t[r];
+            out[i] = s;
+        }
+        __syncthreads();
+    }
+    __device__ void sum32(double (&v)[32], int n, SmemFixed &S, double *out, bool active = true) {
+        double *pt = next_part();
+        block_partials32(v, n, S.red, pt, 1, active, 0);
+        cl.sync();
+        cluster_sum(pt, n, out);
+    }
+    template <class Fill>
+    __device__ void sum_many(int nv, SmemFixed &S, double *out, Fill fill) {
+        double *pt = next_part();
+        for (int c0 = 0; c0 < nv; c0 += 32) {
+            double v[32];
+            fill(c0, v);
+            block_partials32(v, min(32, nv - c0), S.red, pt + c0, 1, true, 0);
+        }
+        cl.sync();
+        cluster_sum(pt, nv, out);
     }
 };
 

@@ -45,12 +45,14 @@ def _surfaces(nx, seed):
     return e1, e1 + 0.002 * np.cos(3 * x + rng.uniform(0, 6))
 
 
+@pytest.mark.parametrize("cluster", [1, 4])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_solve_matches_oracle(sw, precision):
+def test_batch_solve_matches_oracle(sw, precision, cluster):
     kw = dict(restart=20, max_restarts=400, tol=1e-12, guess="cold")
     mem = _members()
     probs = [sw.Problem(nx, 1, nz, L, 0.0, h, precision=precision, **kw) for nx, nz, L, h in mem]
     batch = sw.Batch(probs)
+    batch.set_cluster(cluster)
     eps, ecs, bs, xs, refs = [], [], [], [], []
     for i, (nx, nz, L, h) in enumerate(mem):
         ora = O.OracleProblem(nx, 1, nz, L, 0.0, h, **kw)
@@ -71,7 +73,8 @@ def test_batch_solve_matches_oracle(sw, precision):
         assert err <= 1e-10, (i, err)
 
 
-def test_batch_stage_driver_matches_oracle(sw):
+@pytest.mark.parametrize("cluster", [1, 8])
+def test_batch_stage_driver_matches_oracle(sw, cluster):
     kw = dict(restart=20, max_restarts=200, tol=1e-12, guess="previous")
     wls = [W.airy_2d(nx=64, nz=9), W.airy_2d(nx=32, nz=7, kh=0.7), W.periodic_bar_2d(nx=64, nz=9)]
     probs, oras, states = [], [], []
@@ -83,6 +86,7 @@ def test_batch_stage_driver_matches_oracle(sw):
         oras.append(O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw))
         states.append(W.state_arrays(wl))
     batch = sw.Batch(probs)
+    batch.set_cluster(cluster)
     for step in range(2):
         for i in range(1, 6):
             batch.advance_stage()
@@ -98,7 +102,8 @@ def test_batch_stage_driver_matches_oracle(sw):
                     assert err < 1e-9, (wl["name"], step, i, name, err)
 
 
-def test_batch_ewma_iterations_match_single(sw):
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_batch_ewma_iterations_match_single(sw, cluster):
     kw = dict(restart=20, max_restarts=200, tol=1e-8, guess="ewma", k=6, decay=0.9, n_init_solves=5)
     wls = [W.airy_2d(nx=64, nz=9), W.periodic_bar_2d(nx=64, nz=9)]
     def make():
@@ -111,6 +116,7 @@ def test_batch_ewma_iterations_match_single(sw):
         return ps
     single, batched = make(), make()
     batch = sw.Batch(batched)
+    batch.set_cluster(cluster)
     for _ in range(4 * 5):
         batch.advance_stage()
         for p in single:
