@@ -57,6 +57,10 @@ def lib():
         L.or_ewma_guess.argtypes = [vp, dp, dp]
         L.or_ewma_guess.restype = C.c_int
         L.or_ewma_update.argtypes = [vp, dp, C.c_long]
+        L.or_rrf_sketch.argtypes = [vp, dp]
+        L.or_rrf_sketch.restype = C.c_int
+        L.or_rrf_guess.argtypes = [vp, dp, dp]
+        L.or_rrf_guess.restype = C.c_int
         L.or_get_sketch.argtypes = [vp, dp]
         L.or_set_sketch.argtypes = [vp, dp]
         L.or_solve.argtypes = [vp, vp, vp, dp, dp, C.POINTER(Stats)]
@@ -93,7 +97,8 @@ class Relaxation(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("restart", C.c_int), ("max_restarts", C.c_int), ("tol", C.c_double), ("guess", C.c_int),
-                ("k", C.c_int), ("decay", C.c_double), ("n_init_solves", C.c_int), ("seed", C.c_uint64)]
+                ("k", C.c_int), ("decay", C.c_double), ("n_init_solves", C.c_int), ("seed", C.c_uint64),
+                ("history", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -108,7 +113,7 @@ class Physics(C.Structure):
     _fields_ = [("g", C.c_double), ("rho", C.c_double), ("dt", C.c_double)]
 
 
-GUESS = {"cold": 0, "previous": 1, "ewma": 2}
+GUESS = {"cold": 0, "previous": 1, "ewma": 2, "rrf": 3}
 STATUS = {0: "OK", -1: "BAD_ARG", -3: "NOT_CONVERGED", -4: "SINGULAR", -5: "NAN"}
 
 
@@ -167,10 +172,10 @@ class OracleProblem:
     """One sigma-grid problem: operator, ILU(0), GMRES, EWMA history, stage driver."""
 
     def __init__(self, nx, ny, nz, lx, ly, h, restart=20, max_restarts=50, tol=1e-8, guess="cold", k=10,
-                 decay=0.9, n_init_solves=30, seed=2511, walls=False):
+                 decay=0.9, n_init_solves=30, seed=2511, walls=False, history=15):
         self.grid = Grid(nx, ny, nz, lx, ly if ny > 1 else 0.0, int(bool(walls)))
         self.walls = bool(walls)
-        self.params = Params(restart, max_restarts, tol, GUESS[guess], k, decay, n_init_solves, seed)
+        self.params = Params(restart, max_restarts, tol, GUESS[guess], k, decay, n_init_solves, seed, history)
         st = C.c_int(0)
         h = _f64(h).ravel()
         assert h.size == nx * ny
@@ -269,6 +274,17 @@ class OracleProblem:
         Y = np.zeros(self.m * self.k)
         lib().or_get_sketch(self._p, Y)
         return Y.reshape(self.k, self.m).T.copy()
+
+    def rrf_sketch(self):
+        """Y = X Omega of the range finder for the next solve (m x k_e)."""
+        Y = np.zeros(self.m * self.k)
+        ke = lib().or_rrf_sketch(self._p, Y)
+        return Y[:ke * self.m].reshape(ke, self.m).T.copy()
+
+    def rrf_guess(self, b):
+        x0 = np.zeros(self.m)
+        rank = lib().or_rrf_guess(self._p, _f64(b), x0)
+        return x0, rank
 
     def set_sketch(self, Y):
         lib().or_set_sketch(self._p, _f64(np.asarray(Y).T.ravel()))

@@ -22,6 +22,7 @@ struct or_problem {
     int *diag;           /* position of the diagonal in each row of LU */
     double *Y;           /* EWMA sketch, k columns of length m, column-major */
     double *x_prev;      /* last solution */
+    double *X;           /* range finder: ring of the K newest solutions, slot = solve index mod K */
     long n_solves;
     double *work;        /* scratch */
 };

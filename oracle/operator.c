@@ -378,7 +378,8 @@ or_problem *or_create(const or_grid *g, const or_params *p, const double *h, int
     if (g->nx < 1 || g->ny < 1 || g->nz < OR_W || !(g->lx > 0) || (g->ny > 1 && !(g->ly > 0)))
         return NULL;
     if (g->walls && (g->ny != 1 || g->nx < 16)) return NULL;
-    if (p->restart < 1 || p->k < 0 || p->max_restarts < 0) return NULL;
+    if (p->restart < 1 || p->k < 0 || p->max_restarts < 0 || p->history < 0 || p->k > 64) return NULL;
+    if (p->guess == OR_GUESS_RRF && (p->history < 1 || p->k > p->history)) return NULL;
     or_problem *P = calloc(1, sizeof(or_problem));
     P->g = *g;
     P->p = *p;
@@ -435,6 +436,7 @@ or_problem *or_create(const or_grid *g, const or_params *p, const double *h, int
     or_colgeom_free(&G0);
     P->Y = calloc((size_t)P->m * (p->k > 0 ? p->k : 1), sizeof(double));
     P->x_prev = calloc(P->m, sizeof(double));
+    P->X = calloc((size_t)P->m * (p->history > 0 ? p->history : 1), sizeof(double));
     P->work = malloc((size_t)P->m * 8 * sizeof(double));
     /* Unknown ordering of the factorisation (not fixed by the paper): columns
      * are split into four colours, colour = (ix + iy) mod 4; colour 0
@@ -481,6 +483,6 @@ void or_destroy(or_problem *P)
     free(P->ws1); free(P->ws2); free(P->win);
     free(P->h); free(P->hx); free(P->hy); free(P->hxx); free(P->hyy);
     free(P->order); free(P->rank); free(P->diag);
-    free(P->Y); free(P->x_prev); free(P->work);
+    free(P->Y); free(P->x_prev); free(P->X); free(P->work);
     free(P);
 }

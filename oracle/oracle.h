@@ -32,7 +32,7 @@ extern "C" {
 #define OR_HALF 3
 
 enum { OR_OK = 0, OR_BAD_ARG = -1, OR_NOT_CONVERGED = -3, OR_SINGULAR = -4, OR_NAN = -5 };
-enum { OR_GUESS_COLD = 0, OR_GUESS_PREV = 1, OR_GUESS_EWMA = 2 };
+enum { OR_GUESS_COLD = 0, OR_GUESS_PREV = 1, OR_GUESS_EWMA = 2, OR_GUESS_RRF = 3 };
 
 typedef struct {
     int nx, ny, nz;   /* columns in x and y (ny = 1 in 2D), sigma levels 0..nz-1 (ghost level -1 extra) */
@@ -51,6 +51,7 @@ typedef struct {
     double decay;      /* forgetting factor r applied once per solve */
     int n_init_solves; /* solves that use the previous-solution guess before EWMA starts */
     uint64_t seed;     /* seed of the Gaussian sketch vectors */
+    int history;       /* K: past solutions kept for the randomized range finder (Algorithm 3) */
 } or_params;
 
 typedef struct {
@@ -116,6 +117,13 @@ int or_ewma_guess(or_problem *P, const double *b, double *x0);
 void or_ewma_update(or_problem *P, const double *x, long solve_index);
 void or_get_sketch(const or_problem *P, double *Y);
 void or_set_sketch(or_problem *P, const double *Y);
+/* Randomized range finder (Algorithm 3) with V = Y: Y = X Omega for the K_e = min(solves,
+ * K) newest solutions X (column r = the r-th newest) and Omega = the first K_e rows of the
+ * K x k Gaussian matrix of this solve (entry (r, c) = draw r k + c of or_draw_omega with
+ * K k values); k_e = min(k, K_e) columns.  Writes Y (m x k_e, column-major), returns k_e. */
+int or_rrf_sketch(const or_problem *P, double *Y);
+/* Guess of Algorithm 2 with V = Y of the range finder; returns the numerical rank. */
+int or_rrf_guess(or_problem *P, const double *b, double *x0);
 /* Full solve of Algorithm 2: assemble A(eta_prev, eta_cur), guess, GMRES, history update. */
 int or_solve(or_problem *P, const double *eta_prev, const double *eta_cur, const double *b,
              double *x_out, or_stats *st);

@@ -9,6 +9,9 @@
  *   (the rank-1 form printed below Algorithm 4).  omega ~ N(0, I_k).
  * The age is counted in solves (one decay factor r per solve); see the
  * reading recorded with the decay parameter.
+ * Algorithm 3 (randomized range finder): V = Y = X Omega with X the K newest
+ * solutions and a fresh Gaussian Omega (K x k) for every solve; the optional
+ * orthonormalisation V = Q is not taken (same span in exact arithmetic).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -128,6 +131,45 @@ void or_set_sketch(or_problem *P, const double *Y)
     memcpy(P->Y, Y, (size_t)P->m * P->p.k * sizeof(double));
 }
 
+int or_rrf_sketch(const or_problem *P, double *Y)
+{
+    int m = P->m, k = P->p.k, K = P->p.history;
+    long s = P->n_solves;
+    int Ke = s < K ? (int)s : K;
+    int ke = k < Ke ? k : Ke;
+    double *om = malloc((size_t)K * k * sizeof(double));
+    or_draw_omega(P->p.seed, s, K * k, om);
+    for (int c = 0; c < ke; ++c) {
+        double *yc = Y + (size_t)c * m;
+        for (int i = 0; i < m; ++i) yc[i] = 0.0;
+        for (int r = 0; r < Ke; ++r) {
+            const double *xr = P->X + (size_t)((s - 1 - r) % K) * m;   /* r-th newest solution */
+            const double w = om[r * k + c];
+            for (int i = 0; i < m; ++i) yc[i] += xr[i] * w;
+        }
+    }
+    free(om);
+    return ke;
+}
+
+int or_rrf_guess(or_problem *P, const double *b, double *x0)
+{
+    int m = P->m, k = P->p.k;
+    double *Y = malloc((size_t)m * k * sizeof(double));
+    double *W = malloc((size_t)m * k * sizeof(double));
+    double z[64];
+    int ke = or_rrf_sketch(P, Y);
+    for (int c = 0; c < ke; ++c) or_matvec(P, Y + (size_t)c * m, W + (size_t)c * m);
+    int rank = or_lstsq_qr(m, ke, W, b, z);
+    for (int i = 0; i < m; ++i) {
+        double sum = 0;
+        for (int c = 0; c < ke; ++c) sum += Y[(size_t)c * m + i] * z[c];
+        x0[i] = sum;
+    }
+    free(Y); free(W);
+    return rank;
+}
+
 int or_solve(or_problem *P, const double *eta_prev, const double *eta_cur, const double *b,
              double *x_out, or_stats *st)
 {
@@ -135,13 +177,18 @@ int or_solve(or_problem *P, const double *eta_prev, const double *eta_cur, const
     or_assemble(P, eta_prev, eta_cur);
     long s = P->n_solves;
     int mode = P->p.guess;
-    if (mode == OR_GUESS_EWMA && (s < P->p.n_init_solves || P->p.k == 0)) mode = OR_GUESS_PREV;
+    if ((mode == OR_GUESS_EWMA || mode == OR_GUESS_RRF) && (s < P->p.n_init_solves || P->p.k == 0))
+        mode = OR_GUESS_PREV;
+    if (mode == OR_GUESS_RRF && s == 0) mode = OR_GUESS_PREV;
     if (mode == OR_GUESS_COLD) for (int i = 0; i < m; ++i) x_out[i] = 0.0;
     else if (mode == OR_GUESS_PREV) memcpy(x_out, P->x_prev, m * sizeof(double));
+    else if (mode == OR_GUESS_RRF) or_rrf_guess(P, b, x_out);
     else or_ewma_guess(P, b, x_out);
     int status = or_gmres(P, b, x_out, st);
     memcpy(P->x_prev, x_out, m * sizeof(double));
     if (P->p.guess == OR_GUESS_EWMA && P->p.k > 0) or_ewma_update(P, x_out, s);
+    if (P->p.guess == OR_GUESS_RRF && P->p.history > 0)
+        memcpy(P->X + (size_t)(s % P->p.history) * m, x_out, m * sizeof(double));
     P->n_solves++;
     return status;
 }
