@@ -60,6 +60,9 @@ extern "C" {
 #define SW_GUESS_COLD 0      /* x0 = 0 */
 #define SW_GUESS_PREVIOUS 1  /* x0 = previous solution (the paper's baseline, Sec. 5.1) */
 #define SW_GUESS_EWMA 2      /* Algorithm 4 with V = Y (Algorithm 2) */
+#define SW_GUESS_RRF 3       /* Algorithm 3 (randomized range finder) with V = Y = X Omega over the
+                                `history` newest solutions, a fresh Gaussian Omega per solve */
+#define SW_RRF_MAX_HISTORY 16
 
 #define SW_PRECISION_FP64 0  /* every step in FP64 */
 #define SW_PRECISION_MIXED 1 /* FP32 inner GMRES cycles, FP64 outer residual */
@@ -93,6 +96,7 @@ typedef struct {
     int precision;      /* SW_PRECISION_* */
     uint64_t seed;      /* seed of the Gaussian sketch vectors omega */
     int executor;       /* SW_EXEC_*: how a solve is run on the GPU (same arithmetic) */
+    int history;        /* K of the range finder: solutions kept, k..SW_RRF_MAX_HISTORY (SW_GUESS_RRF) */
 } sw_params;
 
 typedef struct {
@@ -186,7 +190,11 @@ int sw_get_sketch(sw_problem *p, double *d_Y, void *stream);
 int sw_set_sketch(sw_problem *p, const double *d_Y, long long n_solves, void *stream);
 
 /* The Gaussian sketch vector omega of a given solve (host): SplitMix64
- * outputs 2(s k + c) + 1 and 2(s k + c) + 2 through Box-Muller, c = 0..k-1. */
+ * outputs 2(s k + c) + 1 and 2(s k + c) + 2 through Box-Muller, c = 0..k-1.
+ * The range finder's K x k matrix Omega of solve s is the draw with K k
+ * values, entry (r, c) at r k + c, row r weighting the r-th newest solution;
+ * with fewer than K solutions stored, the first K_e rows and min(k, K_e)
+ * columns are used. */
 int sw_draw_omega(uint64_t seed, long long solve_index, int k, double *h_omega);
 
 /* ---- stage driver: Algorithm 1 with LSERK45 (Sec. 3 and Sec. 5) ---- */

@@ -411,8 +411,12 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
         set_error("grid: walls need a 2-D grid with nx >= 16");
         return SW_ERR_BAD_ARG;
     }
+    if (p.guess == SW_GUESS_RRF && (p.history < p.k || p.history > SW_RRF_MAX_HISTORY)) {
+        set_error("params: the range finder needs k <= history <= 16");
+        return SW_ERR_BAD_ARG;
+    }
     if (p.restart < 1 || p.restart > MAX_RESTART || p.max_restarts < 0 || !(p.tol > 0) || p.guess < 0 ||
-        p.guess > 2 || p.k < 1 || p.k > MAX_K || !(p.decay > 0) || p.decay > 1 || p.n_init_solves < 0 ||
+        p.guess > 3 || p.k < 1 || p.k > MAX_K || !(p.decay > 0) || p.decay > 1 || p.n_init_solves < 0 ||
         (p.precision != SW_PRECISION_FP64 && p.precision != SW_PRECISION_MIXED) || p.executor < 0 ||
         p.executor > 2) {
         set_error("params: restart 1..32, k 1..16, decay in (0,1], tol > 0, known guess/precision/executor");
@@ -579,6 +583,7 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     ALLOC(P->d_Y[1], (size_t)p.k * m * sizeof(double));
     ALLOC(P->d_W, (size_t)p.k * m * sizeof(double));
     ALLOC(P->d_xprev, (size_t)m * sizeof(double));
+    if (p.guess == SW_GUESS_RRF) ALLOC(P->d_X, (size_t)p.history * m * sizeof(double));
     ALLOC(P->d_omega, MAX_K * sizeof(double));
     ALLOC(P->d_stats, sizeof(DevStats));
     ALLOC(P->d_host_io, (3 * (size_t)m + 2 * (size_t)H.ncol) * sizeof(double));

@@ -189,12 +189,29 @@ SolveArgs make_args(Problem *P, const double *ep, const double *ec, const double
     // global target); the FP64 residual at each restart does the refinement
     A.inner_rtol = 0.0;
     int mode = pr.guess;
-    if (mode == SW_GUESS_EWMA && P->n_solves < pr.n_init_solves) mode = SW_GUESS_PREVIOUS;
-    if (guess_only) mode = SW_GUESS_EWMA;
+    if ((mode == SW_GUESS_EWMA || mode == SW_GUESS_RRF) && P->n_solves < pr.n_init_solves) mode = SW_GUESS_PREVIOUS;
+    if (mode == SW_GUESS_RRF && P->n_solves == 0) mode = SW_GUESS_PREVIOUS;
+    if (guess_only) mode = pr.guess == SW_GUESS_RRF && P->n_solves > 0 ? SW_GUESS_RRF : SW_GUESS_EWMA;
     A.guess_mode = mode;
     A.cm = P->cost;
     A.pending = P->pending ? 1 : 0;
     if (A.pending) sw_draw_omega(pr.seed, P->n_solves - 1, pr.k, A.omega);
+    if (pr.guess == SW_GUESS_RRF) {
+        const int K = pr.history;
+        A.ring = P->d_X;
+        A.ring_K = K;
+        A.ring_store = guess_only ? nullptr : P->d_X + (size_t)(P->n_solves % K) * P->m;
+        A.ring_Ke = (int)(P->n_solves < K ? P->n_solves : K);
+        A.ring_newest = (int)((P->n_solves + K - 1) % K);
+        if (mode == SW_GUESS_RRF) {
+            // Omega of this solve: K x k, entry (r, c) at r k + c; k_e = min(k, K_e) columns
+            double om[SW_RRF_MAX_HISTORY * MAX_K];
+            sw_draw_omega(pr.seed, P->n_solves, K * pr.k, om);
+            A.k = pr.k < A.ring_Ke ? pr.k : A.ring_Ke;
+            for (int r = 0; r < K; ++r)
+                for (int c = 0; c < A.k; ++c) A.omega_rrf[r * A.k + c] = om[r * pr.k + c];
+        }
+    }
     return A;
 }
 

@@ -159,6 +159,22 @@ __global__ void __launch_bounds__(NTHREADS) sk_norms_b(const double *b, const TI
     block_partials32(v, 2, red, part, gridDim.x);
 }
 
+// Range finder: column c of Y = X Omega over the Ke newest stored solutions
+struct RrfCol {
+    double w[SW_RRF_MAX_HISTORY];   // Omega[r][c], r-th newest solution
+    int Ke, K, newest;
+};
+__global__ void __launch_bounds__(NTHREADS) sk_rrf_y(const double *ring, RrfCol rc, double *Yc, long long m) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r < rc.Ke; ++r) {
+            const int slot = (rc.newest - r + rc.K) % rc.K;
+            s += ring[(size_t)slot * m + p] * rc.w[r];
+        }
+        Yc[p] = s;
+    }
+}
+
 __global__ void __launch_bounds__(NTHREADS) sk_ynew(const double *Yc, const double *xprev, double decay, double om,
                                                      double *Ync, long long m) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x)
@@ -214,7 +230,7 @@ __global__ void __launch_bounds__(NTHREADS) sk_x0(const double *Y, const double 
                                                    int mode, double *x, long long m) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x) {
         double s = 0.0;
-        if (mode == SW_GUESS_EWMA) {
+        if (mode == SW_GUESS_EWMA || mode == SW_GUESS_RRF) {
             for (int c = 0; c < k; ++c) s += Y[(size_t)c * m + p] * ss->z[c];
         } else if (mode == SW_GUESS_PREVIOUS) {
             s = xprev[p];
@@ -342,11 +358,13 @@ __global__ void __launch_bounds__(NTHREADS) sk_update_x(double *x, const TI *V, 
     }
 }
 
-__global__ void __launch_bounds__(NTHREADS) sk_final_x(double *x, double *xprev, long long m, const SState *ss) {
+__global__ void __launch_bounds__(NTHREADS) sk_final_x(double *x, double *xprev, double *ring_store, long long m,
+                                                        const SState *ss) {
     const bool zero = ss->bnorm == 0.0;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x) {
         if (zero) x[p] = 0.0;
         xprev[p] = x[p];
+        if (ring_store) ring_store[p] = x[p];
     }
 }
 
@@ -476,9 +494,10 @@ __global__ void sk_ctl_chol2(const double *part, int nb, SState *ss, CtlArgs c) 
     }
 }
 
-__global__ void sk_ctl_guess_cost(SState *ss, CtlArgs c, int upd) {
+__global__ void sk_ctl_guess_cost(SState *ss, CtlArgs c, int upd, int rrf_Ke) {
     if (threadIdx.x != 0) return;
-    if (c.guess_mode == SW_GUESS_EWMA) {
+    if (c.guess_mode == SW_GUESS_RRF) add_cost(ss, c, 2.0 * rrf_Ke * c.k, (rrf_Ke + c.k) * 8.0);
+    if (c.guess_mode == SW_GUESS_EWMA || c.guess_mode == SW_GUESS_RRF) {
         add_cost(ss, c, 2.0 * c.k, c.k * 8.0 + 8.0);
     } else {
         if (upd) add_cost(ss, c, 3.0 * c.k, (2.0 * c.k + 1.0) * 8.0);
@@ -790,7 +809,19 @@ static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
     launches += 3 + 4 * D.ngroups;
     // a7-a10: guess
     const int upd = A.pending;
-    if (upd || A.guess_mode == SW_GUESS_EWMA) {
+    if (A.guess_mode == SW_GUESS_RRF) {
+        for (int cc = 0; cc < k; ++cc) {
+            RrfCol rc{};
+            for (int r = 0; r < A.ring_Ke; ++r) rc.w[r] = A.omega_rrf[r * k + cc];
+            rc.Ke = A.ring_Ke;
+            rc.K = A.ring_K;
+            rc.newest = A.ring_newest;
+            double *Ync = A.Ynew + (size_t)cc * m;
+            sk_rrf_y<<<SNB, NTHREADS, 0, s>>>(A.ring, rc, Ync, m);
+            sk_apply_w<WM><<<tl.ntiles, NTHREADS, smD, s>>>(D, tl, Ync, A.xprev, 0.0, 0.0, 0, A.Wm + (size_t)cc * m);
+            launches += 2;
+        }
+    } else if (upd || A.guess_mode == SW_GUESS_EWMA) {
         for (int cc = 0; cc < k; ++cc) {
             const double *Yc = A.Yold + (size_t)cc * m;
             double *Ync = A.Ynew + (size_t)cc * m;
@@ -802,8 +833,8 @@ static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
             }
         }
     }
-    const double *Ycur = A.pending ? A.Ynew : A.Yold;
-    if (A.guess_mode == SW_GUESS_EWMA) {
+    const double *Ycur = (A.pending || A.guess_mode == SW_GUESS_RRF) ? A.Ynew : A.Yold;
+    if (A.guess_mode == SW_GUESS_EWMA || A.guess_mode == SW_GUESS_RRF) {
         sk_gram<<<SNB, NTHREADS, 0, s>>>(A.Wm, A.b, m, k, ss, 0, S->partB);
         sk_ctl_chol1<<<1, NTHREADS, 0, s>>>(S->partB, SNB, ss, c, m, upd);
         sk_gram<<<SNB, NTHREADS, 0, s>>>(A.Wm, A.b, m, k, ss, 1, S->partB);
@@ -811,7 +842,7 @@ static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
         launches += 4;
     }
     sk_x0<<<SNB, NTHREADS, 0, s>>>(Ycur, A.xprev, ss, k, A.guess_mode, A.x, m);
-    sk_ctl_guess_cost<<<1, 32, 0, s>>>(ss, c, upd);
+    sk_ctl_guess_cost<<<1, 32, 0, s>>>(ss, c, upd, A.ring_Ke);
     launches += 2;
     if (A.guess_only) {
         sk_ctl_final<<<1, NTHREADS, 0, s>>>(S->partA, S->nbA, ss, c, A.stats, 1);
@@ -852,7 +883,7 @@ static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
         if (e != cudaSuccess) return cuda_fail(e, "streamed cycle launch");
     }
     // true residual ||b - A x|| / ||b|| in FP64; the solution is kept for the next guess
-    sk_final_x<<<SNB, NTHREADS, 0, s>>>(A.x, A.xprev, m, ss);
+    sk_final_x<<<SNB, NTHREADS, 0, s>>>(A.x, A.xprev, A.ring_store, m, ss);
     sk_apply_resid<WM><<<S->nbA, NTHREADS, smD, s>>>(D, tl, A.x, A.b, A.r, S->partA, ss, 0);
     sk_ctl_final<<<1, NTHREADS, 0, s>>>(S->partA, S->nbA, ss, c, A.stats, 0);
     launches += 3;

@@ -108,6 +108,7 @@ struct Problem {
     double *d_Y[2] = {nullptr, nullptr};  // EWMA sketch, double buffered
     double *d_W = nullptr;         // k x m, A Y
     double *d_xprev = nullptr;
+    double *d_X = nullptr;         // range finder: history x m past solutions
     double *d_part = nullptr;      // per-block partial sums
     double *d_omega = nullptr;     // k doubles
     void *d_stats = nullptr;       // DevStats

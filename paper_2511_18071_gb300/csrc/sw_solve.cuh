@@ -37,6 +37,11 @@ struct SolveArgs {
     double inner_rtol;   // inner cycle stop relative to its starting residual (FP32 inner only)
     double omega[MAX_K];
     CostModel cm;
+    // range finder (Algorithm 3): Y = X Omega over the ke newest of K stored solutions
+    const double *ring;       // K x m past solutions, slot = solve index mod K
+    double *ring_store;       // slot that receives this solve's solution (null: none)
+    int ring_K, ring_Ke, ring_newest;   // slots, solutions used, slot of the newest
+    double omega_rrf[SW_RRF_MAX_HISTORY * MAX_K];   // row r (r-th newest) x column c at r k + c
 };
 
 // Phases of a solve, timed between barriers by the team's first thread (profiling aid).
@@ -395,7 +400,29 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
 
     // ---- a7-a10: initial guess (Algorithm 2) ----
     int guess_rank = -1, shifted = 0;
-    if (A.pending || A.guess_mode == SW_GUESS_EWMA) {
+    if (A.guess_mode == SW_GUESS_RRF) {
+        // Algorithm 3: Y = X Omega over the newest solutions, then W = A Y (FP64)
+        cost(2.0 * A.ring_Ke * k, (A.ring_Ke + k) * 8.0);
+        cost(k * A.cm.fA, k * (A.cm.bA + 8.0));
+        for (int c = 0; c < k; ++c) {
+            double *Ync = Ynew + (size_t)c * m;
+            for (long long p = tid; p < m; p += nth) {
+                double s = 0.0;
+                for (int r = 0; r < A.ring_Ke; ++r) {
+                    const int slot = (A.ring_newest - r + A.ring_K) % A.ring_K;
+                    s += A.ring[(size_t)slot * m + p] * A.omega_rrf[r * k + c];
+                }
+                Ync[p] = s;
+            }
+        }
+        tm.sync();
+        for (int c = 0; c < k; ++c) {
+            StVec<double, double> st{Wm + (size_t)c * m};
+            LdVec<double, double> ld{Ynew + (size_t)c * m, 1.0};
+            team_apply<Team, double, WM>(tm, D, A.tl, tiles, ld, st);
+        }
+        tm.sync();
+    } else if (A.pending || A.guess_mode == SW_GUESS_EWMA) {
         // Y_new = r Y_old + x_prev omega^T (Algorithm 4) and W = A Y_new
         const bool upd = A.pending != 0;
         if (upd) cost(3.0 * k, (2.0 * k + 1.0) * 8.0);
@@ -420,8 +447,8 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
         tm.sync();
     }
     tick(PH_GUESS_W);
-    const double *Ycur = A.pending ? Ynew : Yold;
-    if (A.guess_mode == SW_GUESS_EWMA) {
+    const double *Ycur = (A.pending || A.guess_mode == SW_GUESS_RRF) ? Ynew : Yold;
+    if (A.guess_mode == SW_GUESS_EWMA || A.guess_mode == SW_GUESS_RRF) {
         // Gram G = W^T W and c = W^T b (a8)
         const int ng = k * (k + 1) / 2;
         const int nv = ng + k;
@@ -825,7 +852,10 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = 0.0;
         v[0] = st.acc;
-        for (long long p = tid; p < m; p += nth) A.xprev[p] = A.x[p];
+        for (long long p = tid; p < m; p += nth) {
+            A.xprev[p] = A.x[p];
+            if (A.ring_store) A.ring_store[p] = A.x[p];
+        }
         tm.sum32(v, 1, S, S.res);
         true_res = braw > 0.0 ? sqrt(S.res[0]) / braw : sqrt(S.res[0]);
         cost(A.cm.fA + 3.0, A.cm.bA + 24.0);

@@ -139,7 +139,7 @@ def _record(wl, nsteps, **kw):
     return out
 
 
-@pytest.mark.parametrize("guess", ["previous", "ewma"])
+@pytest.mark.parametrize("guess", ["previous", "ewma", "rrf"])
 @pytest.mark.parametrize("executor", ["persistent", "streamed"])
 def test_trajectory_iterations_and_solutions(sw, guess, executor):
     wl = W.airy_2d()
