@@ -17,6 +17,8 @@
 // host enqueues a whole restart cycle and synchronises once per cycle.
 #include <cmath>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "sw_solve.cuh"
 
@@ -131,6 +133,42 @@ __global__ void __launch_bounds__(NTHREADS) sk_ilu_gather(Dev D, int c, const TI
     const long long rows = (long long)group_size<WM>(D, c) * D.P;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x)
         ilu_gather_row<TI, TIn, LOWER, WM>(D, c, r, in, out);
+}
+
+// periodic grids: one kernel per colour and layout, slot selection resolved at compile time
+template <typename TI, typename TIn, bool LOWER, int L, int CC>
+__global__ void __launch_bounds__(NTHREADS) sk_ilu_gather_cc(Dev D, const TIn *in, TI *out, const SState *ss,
+                                                               int skip) {
+    if (skip && (ss->stop || ss->done)) return;
+    const long long rows = (long long)(D.ncol >> 2) * D.P;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x)
+        ilu_gather_row_cc<L, TI, TIn, LOWER, CC>(D, r, in, out);
+}
+
+template <typename TI, typename TIn, bool LOWER, int L>
+static void launch_gather_cc(const Dev &D, int c, int gb, const TIn *in, TI *out, const SState *ss, int skip,
+                             cudaStream_t s) {
+    switch (c) {
+    case 0: sk_ilu_gather_cc<TI, TIn, LOWER, L, 0><<<gb, NTHREADS, 0, s>>>(D, in, out, ss, skip); break;
+    case 1: sk_ilu_gather_cc<TI, TIn, LOWER, L, 1><<<gb, NTHREADS, 0, s>>>(D, in, out, ss, skip); break;
+    case 2: sk_ilu_gather_cc<TI, TIn, LOWER, L, 2><<<gb, NTHREADS, 0, s>>>(D, in, out, ss, skip); break;
+    default: sk_ilu_gather_cc<TI, TIn, LOWER, L, 3><<<gb, NTHREADS, 0, s>>>(D, in, out, ss, skip); break;
+    }
+}
+
+template <typename TI, typename TIn, bool LOWER, int WM>
+static void launch_gather(const Dev &D, int c, int gb, const TIn *in, TI *out, const SState *ss, int skip,
+                          cudaStream_t s) {
+    if (WM == 1) {
+        sk_ilu_gather<TI, TIn, LOWER, WM><<<gb, NTHREADS, 0, s>>>(D, c, in, out, ss, skip);
+        return;
+    }
+    switch (D.layout) {
+    case CROSS2D: launch_gather_cc<TI, TIn, LOWER, CROSS2D>(D, c, gb, in, out, ss, skip, s); break;
+    case BOX2D: launch_gather_cc<TI, TIn, LOWER, BOX2D>(D, c, gb, in, out, ss, skip, s); break;
+    case CROSS3D: launch_gather_cc<TI, TIn, LOWER, CROSS3D>(D, c, gb, in, out, ss, skip, s); break;
+    default: launch_gather_cc<TI, TIn, LOWER, BOX3D>(D, c, gb, in, out, ss, skip, s); break;
+    }
 }
 
 template <typename TI, int WM>
@@ -678,6 +716,66 @@ static cudaError_t set_smem_attrs(const Dev &D, const Tiling &t) {
     return e;
 }
 
+static Tiling tiling_with(const Dev &D, int TX, int TY) {
+    Tiling t{};
+    t.TX = TX;
+    t.TY = D.three_d ? TY : 1;
+    t.HX = t.TX + 2 * HALF;
+    t.HY = D.three_d ? t.TY + 2 * HALF : 1;
+    t.HW = t.HX * t.HY;
+    t.ntx = D.nx / t.TX;
+    t.nty = D.three_d ? D.ny / t.TY : 1;
+    t.ntiles = t.ntx * t.nty;
+    return t;
+}
+
+// Tile autotuner: time the Arnoldi operator kernel (the precision the solves
+// use) for every admissible tile shape on the problem's own buffers, three
+// launches each after one warm-up, and keep the fastest.  The tile shape
+// changes no output value, only the staging of the halos.
+template <typename TI, int WM>
+static Tiling tune_tiles(Problem *P) {
+    const Dev &D = P->dev;
+    Streamed *S = (Streamed *)P->streamed;
+    Tiling best = st_tiling(D);
+    std::vector<std::pair<int, int>> cand;
+    if (!D.three_d) {
+        for (int TX : {8, 16, 32, 64}) cand.push_back({TX, 1});
+    } else {
+        for (int TX : {8, 16, 32})
+            for (int TY : {4, 8, 16}) cand.push_back({TX, TY});
+    }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { (void)cudaGetLastError(); return best; }
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    TI *V = P->params.precision == SW_PRECISION_MIXED ? (TI *)P->d_V32 : (TI *)P->d_V;
+    TI *tw = (TI *)(P->d_work + P->m);
+    float best_ms = 1e30f;
+    for (auto &c : cand) {
+        if (D.nx % c.first || (D.three_d && D.ny % c.second)) continue;
+        Tiling t = tiling_with(D, c.first, c.second);
+        const size_t sm = tile_smem<TI>(D, t);
+        if (sm > 200 * 1024 || t.ntiles < 152) continue;
+        if (cudaFuncSetAttribute(sk_apply_vj<TI, WM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+            cudaSuccess) { (void)cudaGetLastError(); continue; }
+        sk_apply_vj<TI, WM><<<t.ntiles, NTHREADS, sm, cs>>>(D, t, V, 0, S->ss, tw);
+        cudaEventRecord(a, cs);
+        for (int r = 0; r < 3; ++r) sk_apply_vj<TI, WM><<<t.ntiles, NTHREADS, sm, cs>>>(D, t, V, 0, S->ss, tw);
+        cudaEventRecord(b, cs);
+        if (cudaEventSynchronize(b) != cudaSuccess) { (void)cudaGetLastError(); continue; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) { best_ms = ms; best = t; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamDestroy(cs);
+    (void)cudaGetLastError();
+    return best;
+}
+
 int setup_streamed(Problem *P) {
     Streamed *S = new (std::nothrow) Streamed();
     if (!S) { set_error("out of host memory"); return SW_ERR_BAD_ARG; }
@@ -687,12 +785,18 @@ int setup_streamed(Problem *P) {
     S->nbA = S->tl.ntiles < SNB ? S->tl.ntiles : SNB;
     cudaError_t e = cudaMalloc((void **)&S->ss, sizeof(SState));
     if (e == cudaSuccess) { P->allocs.push_back(S->ss); e = cudaMemset(S->ss, 0, sizeof(SState)); }
-    if (e == cudaSuccess) e = cudaMalloc((void **)&S->partA, (size_t)S->nbA * 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S->partA, (size_t)SNB * 2 * sizeof(double));
     if (e == cudaSuccess) P->allocs.push_back(S->partA);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->partB, (size_t)SNB * PART_STRIDE * sizeof(double));
     if (e == cudaSuccess) P->allocs.push_back(S->partB);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_done, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "streamed executor set-up");
+    {
+        const bool f32 = P->params.precision == SW_PRECISION_MIXED;
+        if (D.walls) S->tl = f32 ? tune_tiles<float, 1>(P) : tune_tiles<double, 1>(P);
+        else S->tl = f32 ? tune_tiles<float, 0>(P) : tune_tiles<double, 0>(P);
+        S->nbA = S->tl.ntiles < SNB ? S->tl.ntiles : SNB;
+    }
     if (D.walls) {
         e = set_smem_attrs<double, 1>(D, S->tl);
         if (e == cudaSuccess) e = set_smem_attrs<float, 1>(D, S->tl);
@@ -723,7 +827,7 @@ static void st_ilu(const Problem *P, const TIn *in, TI *out, const SState *ss, i
         const long long rows = (long long)per * D.P;
         const int gb = (int)((rows + NTHREADS - 1) / NTHREADS);
         const int pb = (per * 32 + NTHREADS - 1) / NTHREADS;
-        sk_ilu_gather<TI, TIn, true, WM><<<gb, NTHREADS, 0, s>>>(D, c, in, out, ss, skip);
+        launch_gather<TI, TIn, true, WM>(D, c, gb, in, out, ss, skip, s);
         sk_ilu_product<TI, WM><<<pb, NTHREADS, 0, s>>>(D, c, out, 0, ss, skip);
     }
     for (int c = ng - 1; c >= 0; --c) {
@@ -731,7 +835,7 @@ static void st_ilu(const Problem *P, const TIn *in, TI *out, const SState *ss, i
         const long long rows = (long long)per * D.P;
         const int gb = (int)((rows + NTHREADS - 1) / NTHREADS);
         const int pb = (per * 32 + NTHREADS - 1) / NTHREADS;
-        if (c < ng - 1) sk_ilu_gather<TI, TI, false, WM><<<gb, NTHREADS, 0, s>>>(D, c, out, out, ss, skip);
+        if (c < ng - 1) launch_gather<TI, TI, false, WM>(D, c, gb, out, out, ss, skip, s);
         sk_ilu_product<TI, WM><<<pb, NTHREADS, 0, s>>>(D, c, out, 1, ss, skip);
     }
 }

@@ -446,17 +446,20 @@ __device__ __forceinline__ T off_column_sum_walls(const Dev &D, const T *lu, con
 }
 
 // sum over the off-column slots whose neighbour colour satisfies pick(colour)
-template <int L, typename T, bool LOWER>
+// CC >= 0 fixes the colour at compile time: the slot selection is then static
+// and every remaining load is unconditional, so they can all be in flight.
+template <int L, typename T, bool LOWER, int CC = -1>
 __device__ __forceinline__ T off_column_sum(const Dev &D, const T *lu, const T *vals, int c, int ix, int iy, int j,
                                             long long r) {
     const long long m = D.m;
     const int w0 = D.win[j + 1];
+    const int cc = CC >= 0 ? CC : c;
     T acc = T(0);
 #pragma unroll
     for (int i = 0; i < Off<L>::N; ++i) {
         const int ox = Off<L>::ox(i), oy = Off<L>::oy(i);
-        const int nc = (c + ox + oy) & 3;
-        if (LOWER ? (nc >= c) : (nc <= c)) continue;
+        const int nc = (cc + ox + oy) & 3;
+        if (LOWER ? (nc >= cc) : (nc <= cc)) continue;
         const int lev = Off<L>::kk(i) < 0 ? j : w0 + Off<L>::kk(i);
         const int gx = wrapi(ix + ox, D.nx);
         const int gy = (L == CROSS3D || L == BOX3D) ? wrapi(iy + oy, D.ny) : 0;
@@ -605,6 +608,18 @@ __device__ inline void ilu_gather_row_t(const Dev &D, int c, long long row, cons
     const T rhs = LOWER ? T(in[node]) : out[node];
     out[node] = rhs - off_sum<L, T, LOWER, WALLS>(D, lu_ptr<T>(D), out, c, ix, iy, j, fac_row<WALLS>(D, c, q, j));
 }
+// Periodic grids, colour CC known at compile time (row-parallel gather of the streamed executor).
+template <int L, typename T, typename TI, bool LOWER, int CC>
+__device__ inline void ilu_gather_row_cc(const Dev &D, long long row, const TI *in, T *out) {
+    const int per = D.ncol >> 2;
+    const int q = (int)(row % per), j = (int)(row / per) - 1;
+    const int col = col_of<false>(D, CC, q);
+    const int ix = col % D.nx, iy = col / D.nx;
+    const long long node = (long long)(j + 1) * D.ncol + col;
+    const T rhs = LOWER ? T(in[node]) : out[node];
+    out[node] = rhs - off_column_sum<L, T, LOWER, CC>(D, lu_ptr<T>(D), out, CC, ix, iy, j, fac_row<false>(D, CC, q, j));
+}
+
 template <typename T, typename TI, bool LOWER, int WM = 2>
 __device__ inline void ilu_gather_row(const Dev &D, int c, long long row, const TI *in, T *out) {
     if (walls_of<WM>(D)) {
