@@ -56,3 +56,24 @@ def test_omega_matches_oracle_bit_for_bit(sw):
             a = sw.draw_omega(seed, s, 16)
             b = O.draw_omega(seed, s, 16)
             assert np.array_equal(a, b), (seed, s, a - b)
+
+
+def test_new_parameters_rejected_on_host(sw):
+    g = sw.Grid(32, 1, 9, 1.0, 0.0)
+    h = np.ones(32)
+    bad = [
+        sw.Params(20, 5, 1e-8, 3, 10, 0.9, 0, 0, 1, 0, 5),    # range finder: history below k
+        sw.Params(20, 5, 1e-8, 3, 4, 0.9, 0, 0, 1, 0, 17),    # range finder: history above 16
+        sw.Params(20, 5, 1e-8, 4, 4, 0.9, 0, 0, 1, 0, 15),    # unknown guess
+        sw.Params(20, 5, 1e-8, 2, 4, 0.9, 0, 0, 1, 7, 15),    # unknown executor
+    ]
+    for p in bad:
+        with pytest.raises(sw.SawaveError) as e:
+            sw.create_problem(g, p, h)
+        assert e.value.code == -1
+    ok = sw.Params(20, 5, 1e-8, 2, 4, 0.9, 0, 0, 1, 0, 15)
+    for grid, depth in [(sw.Grid(16, 8, 9, 1.0, 1.0, 1), np.ones(128)),   # walls are 2-D only
+                        (sw.Grid(12, 1, 9, 1.0, 0.0, 1), np.ones(12))]:   # walls need nx >= 16
+        with pytest.raises(sw.SawaveError) as e:
+            sw.create_problem(grid, ok, depth)
+        assert e.value.code == -1
