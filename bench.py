@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--members", type=int, default=512, help="batch512: number of instances")
     ap.add_argument("--clusters", default="1,4,8", help="batch512: thread blocks per member to measure")
     ap.add_argument("--spinup", type=int, default=800, help="flume2048: steps from rest before timing")
+    ap.add_argument("--n3d", type=int, default=256, help="bumpy3d: nx = ny (512 for the roofline size)")
     ap.add_argument("--executor", default="auto", choices=["auto", "persistent", "streamed"],
                     help="how a solve runs: auto (by size), persistent kernel, or streamed kernels")
     ap.add_argument("--workload", default="stokes512",
@@ -425,7 +426,7 @@ def bumpy3d_arm(args):
     ge.build()
     import paper_2511_18071_gb300 as sw
     dev = torch.device("cuda", 0)
-    wl = W.bumpy_3d()
+    wl = W.bumpy_3d(nx=args.n3d, ny=args.n3d)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     res = {}
     last = {}
@@ -469,7 +470,8 @@ def bumpy3d_arm(args):
             "roofline": {"kernel": "solve_kernel<float>", "bound": "hbm", "achieved": ach,
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": ach / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None, "traffic": None},
-            "config": {"workload": "bumpy3d_256x256x17", "unknowns": wl["m"], "guess": "ewma", "k": args.k,
+            "config": {"workload": "bumpy3d_%dx%dx17" % (args.n3d, args.n3d), "unknowns": wl["m"], "guess": "ewma",
+                       "k": args.k,
                        "executor": args.executor,
                        "decay": args.decay, "tol": 1e-8, "restart": 20,
                        "l2": "inputs larger than L2 and flushed between timed steps"}}

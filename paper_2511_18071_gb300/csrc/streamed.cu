@@ -42,31 +42,33 @@ struct SState {
 
 // ---- reductions ----------------------------------------------------------
 
+// One block: out[i] = sum over b < nb of part[i * nb + b], i < n (fixed order).
+__device__ inline void reduce_parts(const double *part, int n, int nb, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < n; i += NWARPS) {
+        // four independent accumulators keep four loads in flight per lane
+        const double *pi = part + (size_t)i * nb;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int b = lane;
+        for (; b + 96 < nb; b += 128) {
+            s0 += pi[b];
+            s1 += pi[b + 32];
+            s2 += pi[b + 64];
+            s3 += pi[b + 96];
+        }
+        for (; b < nb; b += 32) s0 += pi[b];
+        double s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[i] = s;
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ void zero32(double (&v)[32]) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = 0.0;
 }
-
-// One block: out[i] = sum over b < nb of part[i * nb + b], i < n, in a fixed
-// order.  Every thread takes a stride of blocks for all values at once (all
-// its loads independent), then one block reduction finishes each chunk of 32.
-__device__ inline void reduce_parts(const double *part, int n, int nb, double *out) {
-    __shared__ double red[NWARPS * 32];
-    for (int c0 = 0; c0 < n; c0 += 32) {
-        const int nc = min(32, n - c0);
-        double v[32];
-        zero32(v);
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                if (i >= nc) break;
-                v[i] += part[(size_t)(c0 + i) * nb + b];
-            }
-        }
-        block_partials32(v, nc, red, out + c0, 1, true, 0);
-    }
-}
-
 
 // ---- operator kernels ------------------------------------------------------
 
