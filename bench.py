@@ -35,8 +35,8 @@ WORKLOAD = "stokes2d_512x17_kh2_a1h0.08"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default per workload)")
+    ap.add_argument("--warmup", type=int, default=None, help="untimed warm-up steps (default per workload)")
     ap.add_argument("--impl", default="sawave", choices=["sawave", "reference"])
     ap.add_argument("--decay", type=float, default=0.9)
     ap.add_argument("--k", type=int, default=10)
@@ -55,7 +55,19 @@ def parse():
                          "precision form vs FP64; batch512: 512 uneven instances, batched vs one by one; "
                          "flume2048: 2048 x 17 flume over the bar with walls and relaxation zones (FP64); "
                          "decay_sweep: the headline workload with EWMA decay r in {0.8, 0.9, 0.95, 1.0}")
-    return ap.parse_args()
+    a = ap.parse_args()
+    # defaults per workload, each run finishing in minutes: the headline and its
+    # decay sweep 40 timed steps after 8; the 3-D field 3 after 3; the batch one
+    # step after 7 (past the 30 previous-solution solves that fill the history)
+    steps, warm = {"stokes512": (40, 8), "decay_sweep": (40, 8), "flume2048": (40, 8), "bumpy3d": (3, 3),
+                   "batch512": (1, 7)}[a.workload]
+    if a.steps is None:
+        a.steps = steps
+    if a.warmup is None:
+        a.warmup = warm
+    if a.workload == "batch512" and a.clusters == "1,4,8":
+        a.clusters = "16"
+    return a
 
 
 def workload():
