@@ -13,7 +13,8 @@ seven-group factorisation order, and the generation/absorption zones.
    a whole group at once); GMRES reaches the dense solution.
 4. A closed basin one wavelength long, started at rest from a cos(kx), is a
    standing wave: after half a period the surface is -a cos(kx), after a full
-   period a cos(kx) again (linear theory), within 1 % of a.
+   period a cos(kx) again (linear theory), within 1 % of a; the volume under
+   the surface is conserved (no flux through the walls).
 5. Relaxation zones: weight Gamma(0) = 1, Gamma(1) = 0, monotone; the linear
    dispersion relation is solved to rounding; a flume driven by the
    generation zone carries the incident linear wave between the zones with
@@ -242,6 +243,13 @@ def test_closed_basin_standing_wave():
     a = 0.002
     phys = slice(1, wl["nx"] - 1)
     n = wl["steps"]
+    dx = wl["lx"] / (wl["nx"] - 3)
+
+    def mass(eta):   # trapezoid rule over the physical columns, wall to wall
+        e = eta[phys]
+        return dx * (e.sum() - 0.5 * (e[0] + e[-1]))
+
+    m0 = mass(st["eta"])
     snaps = {}
     for step in range(n):
         for i in range(1, 6):
@@ -252,6 +260,8 @@ def test_closed_basin_standing_wave():
     ref = a * np.cos(wl["k"] * x)
     assert np.abs(snaps[n // 2][phys] + ref[phys]).max() < 0.01 * a, np.abs(snaps[n // 2][phys] + ref[phys]).max()
     assert np.abs(snaps[n][phys] - ref[phys]).max() < 0.01 * a, np.abs(snaps[n][phys] - ref[phys]).max()
+    # no flux through the walls: the volume of the surface stays put (to 1e-6 of a L)
+    assert abs(mass(st["eta"]) - m0) < 1e-6 * a * wl["lx"], mass(st["eta"]) - m0
     # no flow through the walls: the wall-node horizontal velocity stays at rounding level
     u = st["u"].reshape(wl["nz"] + 1, wl["nx"])
     assert np.abs(u[1:, 1]).max() < 1e-3 * a * wl["omega"] / wl["k"], np.abs(u[1:, 1]).max()
