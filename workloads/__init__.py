@@ -6,9 +6,10 @@ and time step of each workload.  It contains none of the solver's arithmetic
 and is shared by the tests, the benchmark and the oracle checks.
 
 Stand-ins: the paper initialises stream-function waves from Fenton's Fourier
-method and runs the Beji-Battjes flume (Sec. 5); neither Fenton's solutions
-nor the flume data are available here, so the workloads below use sums of
-linear waves of the same wavenumber, depth and steepness class instead.
+method and runs the Beji-Battjes flume (Sec. 5).  The stream-function waves
+are computed here (workloads.stream_function, Fenton's method written out);
+the flume's measured data are not available, and the other workloads use sums
+of linear waves of the same wavenumber, depth and steepness class.
 """
 import math
 
@@ -247,3 +248,21 @@ def standing_wave_basin(nx=67, nz=9, depth=1.0, kh=1.0, a_over_h=0.01, steps=128
     return dict(name="basin2d_%dx%d" % (nx, nz), nx=nx, ny=1, nz=nz, lx=lx, ly=0.0, h=h,
                 eta=a_over_h * depth * np.cos(k * x), u=np.zeros(m), v=None, w=np.zeros(m), dt=T / steps,
                 steps=steps, g=G, rho=RHO, m=m, walls=True, relax=None, k=k, omega=float(om))
+
+
+def stream_function_2d(nx=200, nz=20, kh=1.0, steepness=0.6, depth=1.0, steps=200):
+    """Periodic flat-bed slice one wavelength long holding a steady stream-function
+    wave (Sec. 5.1): height H = steepness (H/L)_max L with Battjes' limit, crest at
+    x = 0, no mean Eulerian current; nx x nz = 200 x 20 as in the paper's study."""
+    from .stream_function import battjes_max_steepness, converged_wave, stream_function_fields
+    k = kh / depth
+    lx = 2 * math.pi / k
+    x = np.arange(nx) * (lx / nx)
+    h = np.full(nx, depth)
+    h_over_l = steepness * battjes_max_steepness(kh)
+    wave = converged_wave(kh, 2 * math.pi * h_over_l)
+    eta, u, w = stream_function_fields(x, depth, nz, wave, k, G)
+    dt = courant_dt(lx / nx, lx, depth)
+    return dict(name="sfwave2d_%dx%d_kh%g_s%g" % (nx, nz, kh, steepness), nx=nx, ny=1, nz=nz, lx=lx, ly=0.0,
+                h=h, eta=eta, u=u, v=None, w=w, dt=dt, steps=steps, g=G, rho=RHO, m=nx * (nz + 1),
+                kh=kh, steepness=steepness, height=h_over_l * lx, c=wave.c * math.sqrt(G / k), wave=wave)
