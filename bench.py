@@ -50,17 +50,19 @@ def parse():
     ap.add_argument("--executor", default="auto", choices=["auto", "persistent", "streamed"],
                     help="how a solve runs: auto (by size), persistent kernel, or streamed kernels")
     ap.add_argument("--workload", default="stokes512",
-                    choices=["stokes512", "bumpy3d", "batch512", "flume2048", "decay_sweep"],
+                    choices=["stokes512", "bumpy3d", "batch512", "flume2048", "decay_sweep", "sf_sweep"],
                     help="stokes512: the headline 512 x 17 steep wave (FP64); bumpy3d: 256 x 256 x 17 "
                          "precision form vs FP64; batch512: 512 uneven instances, batched vs one by one; "
                          "flume2048: 2048 x 17 flume over the bar with walls and relaxation zones (FP64); "
-                         "decay_sweep: the headline workload with EWMA decay r in {0.8, 0.9, 0.95, 1.0}")
+                         "decay_sweep: the headline workload with EWMA decay r in {0.8, 0.9, 0.95, 1.0}; "
+                         "sf_sweep: stream-function waves over kh x steepness (200 x 20), previous solution vs "
+                         "range finder vs EWMA")
     a = ap.parse_args()
     # defaults per workload, each run finishing in minutes: the headline and its
     # decay sweep 40 timed steps after 8; the 3-D field 3 after 3; the batch one
     # step after 7 (past the 30 previous-solution solves that fill the history)
     steps, warm = {"stokes512": (40, 8), "decay_sweep": (40, 8), "flume2048": (40, 8), "bumpy3d": (3, 3),
-                   "batch512": (1, 7)}[a.workload]
+                   "batch512": (1, 7), "sf_sweep": (200, 6)}[a.workload]
     if a.steps is None:
         a.steps = steps
     if a.warmup is None:
@@ -662,8 +664,65 @@ def decay_sweep_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def sf_sweep_arm(args):
+    """Stream-function waves over the kh x steepness grid of the paper's study
+    (200 x 20 periodic slice, dt = 1e-4 sqrt(h/g), six untimed steps on the previous
+    solution, then the timed steps): previous solution vs the range finder
+    (K = 15, k = 10, V = X Omega) vs EWMA (k = 10, r = 0.7)."""
+    import torch
+
+    import __graft_entry__ as ge
+    import workloads as W
+    ge.build()
+    import paper_2511_18071_gb300 as sw
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    a = argparse.Namespace(**dict(vars(args), k=10, decay=0.7))
+    cases = []
+    tot_solves = tot_ms = 0.0
+    with ClockSampler(0) as clk:
+        for steep in (0.01, 0.3, 0.7):
+            for kh in (0.4, 2.0, 4.0):
+                wl = W.stream_function_2d(kh=kh, steepness=steep, dt_tau=1e-4)
+                row = {"kh": kh, "steepness_of_max": steep, "H_over_L": wl["height"] / wl["lx"],
+                       "fourier_modes": wl["wave"].N}
+                for guess in ("previous", "rrf", "ewma"):
+                    kw = solver_kw(a, guess)
+                    if guess == "rrf":
+                        kw["history"] = 15
+                    P = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], precision="fp64", **kw)
+                    sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+                    sw.set_state(P.handle, _t(torch, dev, wl["u"]), None, _t(torch, dev, wl["w"]),
+                                 _t(torch, dev, wl["eta"]))
+                    run_steps(sw, torch, P, args.warmup)
+                    torch.cuda.synchronize()
+                    r = _timed_steps(sw, torch, P, args.steps, flush)
+                    P.close()
+                    row[guess] = {"iters_per_step": 5 * r["iters_per_solve"], "ms_per_step": r["ms_per_step"],
+                                  "solves_per_s": r["value"]}
+                    if guess == "ewma":
+                        tot_solves += 5 * args.steps
+                        tot_ms += r["ms_per_step"] * args.steps
+                for guess in ("rrf", "ewma"):
+                    row[guess]["iter_speedup"] = row["previous"]["iters_per_step"] / row[guess]["iters_per_step"] \
+                        if row[guess]["iters_per_step"] else None
+                    row[guess]["time_speedup"] = row["previous"]["ms_per_step"] / row[guess]["ms_per_step"]
+                cases.append(row)
+    line = {"metric": METRIC, "value": tot_solves / (tot_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (stream-function waves by Fenton's method)", "clocks": clk.summary(),
+            "value_is": "EWMA solves/s over all nine cases", "cases": cases,
+            "config": {"workload": "sfwave2d_200x20 kh x steepness grid", "unknowns": 4200, "dt_tau": 1e-4,
+                       "tol": 1e-8, "restart": 20, "init_steps_previous": 6, "K": 15, "k": 10, "decay": 0.7,
+                       "l2": "flushed between timed steps (256 MiB write, outside the step events)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "sf_sweep":
+        sf_sweep_arm(args)
+        return
     if args.workload == "flume2048":
         flume2048_arm(args)
         return
