@@ -61,6 +61,8 @@ def lib():
         L.or_rrf_sketch.restype = C.c_int
         L.or_rrf_guess.argtypes = [vp, dp, dp]
         L.or_rrf_guess.restype = C.c_int
+        L.or_orth_basis.argtypes = [C.c_int, C.c_int, dp, dp]
+        L.or_orth_basis.restype = C.c_int
         L.or_get_sketch.argtypes = [vp, dp]
         L.or_set_sketch.argtypes = [vp, dp]
         L.or_solve.argtypes = [vp, vp, vp, dp, dp, C.POINTER(Stats)]
@@ -98,7 +100,7 @@ class Relaxation(C.Structure):
 class Params(C.Structure):
     _fields_ = [("restart", C.c_int), ("max_restarts", C.c_int), ("tol", C.c_double), ("guess", C.c_int),
                 ("k", C.c_int), ("decay", C.c_double), ("n_init_solves", C.c_int), ("seed", C.c_uint64),
-                ("history", C.c_int)]
+                ("history", C.c_int), ("orthonormalize", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -154,6 +156,15 @@ def lstsq_qr(W, b):
     return z, rank
 
 
+def orth_basis(Y):
+    """Orthonormal basis of span(Y) (Gram-Schmidt twice, dependent columns dropped): (Q, r)."""
+    Y = np.asfortranarray(Y, dtype=np.float64)
+    m, k = Y.shape
+    Q = np.zeros(m * max(k, 1))
+    r = lib().or_orth_basis(m, k, _f64(Y.ravel(order="F")), Q)
+    return Q[:m * r].reshape(r, m).T.copy(), r
+
+
 def relax_weight(xi):
     return lib().or_relax_weight(float(xi))
 
@@ -172,10 +183,11 @@ class OracleProblem:
     """One sigma-grid problem: operator, ILU(0), GMRES, EWMA history, stage driver."""
 
     def __init__(self, nx, ny, nz, lx, ly, h, restart=20, max_restarts=50, tol=1e-8, guess="cold", k=10,
-                 decay=0.9, n_init_solves=30, seed=2511, walls=False, history=15):
+                 decay=0.9, n_init_solves=30, seed=2511, walls=False, history=15, orthonormalize=False):
         self.grid = Grid(nx, ny, nz, lx, ly if ny > 1 else 0.0, int(bool(walls)))
         self.walls = bool(walls)
-        self.params = Params(restart, max_restarts, tol, GUESS[guess], k, decay, n_init_solves, seed, history)
+        self.params = Params(restart, max_restarts, tol, GUESS[guess], k, decay, n_init_solves, seed, history,
+                             int(bool(orthonormalize)))
         st = C.c_int(0)
         h = _f64(h).ravel()
         assert h.size == nx * ny

@@ -380,6 +380,7 @@ or_problem *or_create(const or_grid *g, const or_params *p, const double *h, int
     if (g->walls && (g->ny != 1 || g->nx < 16)) return NULL;
     if (p->restart < 1 || p->k < 0 || p->max_restarts < 0 || p->history < 0 || p->k > 64) return NULL;
     if (p->guess == OR_GUESS_RRF && (p->history < 1 || p->k > p->history)) return NULL;
+    if (p->orthonormalize != 0 && p->orthonormalize != 1) return NULL;
     or_problem *P = calloc(1, sizeof(or_problem));
     P->g = *g;
     P->p = *p;

@@ -52,6 +52,8 @@ typedef struct {
     int n_init_solves; /* solves that use the previous-solution guess before EWMA starts */
     uint64_t seed;     /* seed of the Gaussian sketch vectors */
     int history;       /* K: past solutions kept for the randomized range finder (Algorithm 3) */
+    int orthonormalize;/* 1: V = Q, an orthonormal basis of the sketch's span (the optional QR step of
+                          Algorithms 3 and 4); 0: V = Y */
 } or_params;
 
 typedef struct {
@@ -124,6 +126,10 @@ void or_set_sketch(or_problem *P, const double *Y);
 int or_rrf_sketch(const or_problem *P, double *Y);
 /* Guess of Algorithm 2 with V = Y of the range finder; returns the numerical rank. */
 int or_rrf_guess(or_problem *P, const double *b, double *x0);
+/* Orthonormal basis Q (m x r, column-major) of the span of Y (m x k): the Q of
+ * Y = Q R by classical Gram-Schmidt applied twice per column, dropping columns
+ * whose remainder is below 1e-12 of the largest column norm.  Returns r. */
+int or_orth_basis(int m, int k, const double *Y, double *Q);
 /* Full solve of Algorithm 2: assemble A(eta_prev, eta_cur), guess, GMRES, history update. */
 int or_solve(or_problem *P, const double *eta_prev, const double *eta_cur, const double *b,
              double *x_out, or_stats *st);

@@ -9,9 +9,12 @@
  *   (the rank-1 form printed below Algorithm 4).  omega ~ N(0, I_k).
  * The age is counted in solves (one decay factor r per solve); see the
  * reading recorded with the decay parameter.
- * Algorithm 3 (randomized range finder): V = Y = X Omega with X the K newest
- * solutions and a fresh Gaussian Omega (K x k) for every solve; the optional
- * orthonormalisation V = Q is not taken (same span in exact arithmetic).
+ * Algorithm 3 (randomized range finder): Y = X Omega with X the K newest
+ * solutions and a fresh Gaussian Omega (K x k) for every solve.
+ * Both sketches are used as V = Y, or, with the parameter orthonormalize, as
+ * V = Q from the QR factorisation Y = Q R (the optional step of both
+ * algorithms): the same span, so the same x0 in exact arithmetic, but a
+ * well-conditioned basis when the columns of Y are nearly dependent.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -94,20 +97,69 @@ int or_lstsq_qr(int m, int k, const double *W, const double *b, double *z)
     return rank;
 }
 
-int or_ewma_guess(or_problem *P, const double *b, double *x0)
+int or_orth_basis(int m, int k, const double *Y, double *Q)
 {
-    int m = P->m, k = P->p.k;
-    double *W = malloc((size_t)m * k * sizeof(double));
+    double ymax = 0.0;
+    for (int c = 0; c < k; ++c) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += Y[(size_t)c * m + i] * Y[(size_t)c * m + i];
+        if (sqrt(s) > ymax) ymax = sqrt(s);
+    }
+    int r = 0;
+    for (int c = 0; c < k; ++c) {
+        double *q = Q + (size_t)r * m;
+        memcpy(q, Y + (size_t)c * m, m * sizeof(double));
+        for (int pass = 0; pass < 2; ++pass) {          /* q <- q - Q_r (Q_r^T q), twice */
+            double proj[64];
+            for (int l = 0; l < r; ++l) {
+                double s = 0.0;
+                for (int i = 0; i < m; ++i) s += Q[(size_t)l * m + i] * q[i];
+                proj[l] = s;
+            }
+            for (int l = 0; l < r; ++l)
+                for (int i = 0; i < m; ++i) q[i] -= proj[l] * Q[(size_t)l * m + i];
+        }
+        double nq = 0.0;
+        for (int i = 0; i < m; ++i) nq += q[i] * q[i];
+        nq = sqrt(nq);
+        if (!(nq > 1e-12 * ymax)) continue;             /* dependent on the kept columns */
+        for (int i = 0; i < m; ++i) q[i] /= nq;
+        r++;
+    }
+    return r;
+}
+
+/* Algorithm 2 on a basis V (m x kv): z* = argmin ||A V z - b||, x0 = V z*. */
+static int guess_from_basis(or_problem *P, const double *V, int kv, const double *b, double *x0)
+{
+    int m = P->m;
+    double *W = malloc((size_t)m * (kv > 0 ? kv : 1) * sizeof(double));
     double z[64];
-    for (int c = 0; c < k; ++c) or_matvec(P, P->Y + (size_t)c * m, W + (size_t)c * m);
-    int rank = or_lstsq_qr(m, k, W, b, z);
+    for (int c = 0; c < kv; ++c) or_matvec(P, V + (size_t)c * m, W + (size_t)c * m);
+    int rank = kv > 0 ? or_lstsq_qr(m, kv, W, b, z) : 0;
     for (int i = 0; i < m; ++i) {
         double s = 0;
-        for (int c = 0; c < k; ++c) s += P->Y[(size_t)c * m + i] * z[c];
+        for (int c = 0; c < kv; ++c) s += V[(size_t)c * m + i] * z[c];
         x0[i] = s;
     }
     free(W);
     return rank;
+}
+
+/* V = Y, or V = Q of Y = Q R when the problem asks for the orthonormalisation. */
+static int guess_from_sketch(or_problem *P, const double *Y, int kc, const double *b, double *x0)
+{
+    if (!P->p.orthonormalize) return guess_from_basis(P, Y, kc, b, x0);
+    double *Q = malloc((size_t)P->m * (kc > 0 ? kc : 1) * sizeof(double));
+    int r = or_orth_basis(P->m, kc, Y, Q);
+    int rank = guess_from_basis(P, Q, r, b, x0);
+    free(Q);
+    return rank;
+}
+
+int or_ewma_guess(or_problem *P, const double *b, double *x0)
+{
+    return guess_from_sketch(P, P->Y, P->p.k, b, x0);
 }
 
 void or_ewma_update(or_problem *P, const double *x, long solve_index)
@@ -154,19 +206,10 @@ int or_rrf_sketch(const or_problem *P, double *Y)
 
 int or_rrf_guess(or_problem *P, const double *b, double *x0)
 {
-    int m = P->m, k = P->p.k;
-    double *Y = malloc((size_t)m * k * sizeof(double));
-    double *W = malloc((size_t)m * k * sizeof(double));
-    double z[64];
+    double *Y = malloc((size_t)P->m * P->p.k * sizeof(double));
     int ke = or_rrf_sketch(P, Y);
-    for (int c = 0; c < ke; ++c) or_matvec(P, Y + (size_t)c * m, W + (size_t)c * m);
-    int rank = or_lstsq_qr(m, ke, W, b, z);
-    for (int i = 0; i < m; ++i) {
-        double sum = 0;
-        for (int c = 0; c < ke; ++c) sum += Y[(size_t)c * m + i] * z[c];
-        x0[i] = sum;
-    }
-    free(Y); free(W);
+    int rank = guess_from_sketch(P, Y, ke, b, x0);
+    free(Y);
     return rank;
 }
 
