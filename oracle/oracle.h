@@ -15,7 +15,10 @@
  *   - ILU(0) of A at still water and its triangular solves (Sec. 3) .... krylov.c
  *   - left-preconditioned restarted GMRES with CGS2 (Sec. 3) ........... krylov.c
  *   - EWMA sketch and least-squares guess (Algorithms 2 and 4) ......... subspace.c
+ *   - randomized range finder over the K newest solutions (Algorithm 3)  subspace.c
+ *   - optional orthonormal basis V = Q of either sketch ................ subspace.c
  *   - counter-based Gaussian draws for the sketch vectors .............. subspace.c
+ *   - vertical walls with ghost columns and relaxation zones (Sec. 5.2)  operator.c, physics.c
  *   - LSERK45 stage driver, Eq. (14)-(17) and Algorithm 1 .............. physics.c
  *
  * Parity status of each function is listed in oracle/README.md.
