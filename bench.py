@@ -666,7 +666,7 @@ def decay_sweep_arm(args):
 
 def sf_sweep_arm(args):
     """Stream-function waves over the kh x steepness grid of the paper's study
-    (200 x 20 periodic slice, dt = 1e-4 sqrt(h/g), six untimed steps on the previous
+    (200 x 20 periodic slice, dt = 1e-4 s, six untimed steps on the previous
     solution, then the timed steps): previous solution vs the range finder
     (K = 15, k = 10, V = X Omega) vs EWMA (k = 10, r = 0.7)."""
     import torch
@@ -683,7 +683,7 @@ def sf_sweep_arm(args):
     with ClockSampler(0) as clk:
         for steep in (0.01, 0.3, 0.7):
             for kh in (0.4, 2.0, 4.0):
-                wl = W.stream_function_2d(kh=kh, steepness=steep, dt_tau=1e-4)
+                wl = W.stream_function_2d(kh=kh, steepness=steep, dt=1e-4)
                 row = {"kh": kh, "steepness_of_max": steep, "H_over_L": wl["height"] / wl["lx"],
                        "fourier_modes": wl["wave"].N}
                 for guess in ("previous", "rrf", "ewma"):
@@ -712,7 +712,7 @@ def sf_sweep_arm(args):
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (stream-function waves by Fenton's method)", "clocks": clk.summary(),
             "value_is": "EWMA solves/s over all nine cases", "cases": cases,
-            "config": {"workload": "sfwave2d_200x20 kh x steepness grid", "unknowns": 4200, "dt_tau": 1e-4,
+            "config": {"workload": "sfwave2d_200x20 kh x steepness grid", "unknowns": 4200, "dt_s": 1e-4,
                        "tol": 1e-8, "restart": 20, "init_steps_previous": 6, "K": 15, "k": 10, "decay": 0.7,
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)"}}
     print(json.dumps(line), flush=True)

@@ -1,7 +1,8 @@
 """GPU parity on the paper's stream-function wave runs (Sec. 5.1: a periodic
-200 x 20 slice, dt = 1e-4 sqrt(h/g), K = 15, k = 10, r = 0.7, six steps on the
-previous solution before the subspace guess): the library's stage driver,
-through the C ABI, against the oracle's on the same Fenton initial condition.
+200 x 20 slice, K = 15, k = 10, r = 0.7, six steps on the previous solution
+before the subspace guess; here with a step of 3.19e-5 s, a third of the
+paper's): the library's stage driver, through the C ABI, against the oracle's
+on the same Fenton initial condition.
 
 Tolerances: with solves to 1e-12 the fields agree to 1e-9 relative after
 every stage (as in test_gpu_parity.py).  With the paper's 1e-8 the fields agree
@@ -12,6 +13,8 @@ perturbed by 1e-10 relative changes single solves by up to 19 iterations and
 the mean by 4 %); the exact per-solve comparison on shared systems is the Airy
 trajectory test of test_gpu_parity.py.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -22,6 +25,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda"
+DT = 1e-4 * math.sqrt(1.0 / 9.81)
 
 
 @pytest.fixture(scope="module")
@@ -70,7 +74,7 @@ def _run(sw, wl, nsteps, kw, executor, every_stage, tol):
 @pytest.mark.parametrize("kh,steep", [(0.4, 0.7), (2.0, 0.7), (4.0, 0.3)])
 @pytest.mark.parametrize("executor", ["persistent", "streamed"])
 def test_stage_driver_tight(sw, kh, steep, executor):
-    wl = W.stream_function_2d(kh=kh, steepness=steep, dt_tau=1e-4)
+    wl = W.stream_function_2d(kh=kh, steepness=steep, dt=DT)
     kw = dict(restart=20, max_restarts=200, tol=1e-12, guess="previous")
     _run(sw, wl, 2, kw, executor, True, 1e-9)
 
@@ -78,7 +82,7 @@ def test_stage_driver_tight(sw, kh, steep, executor):
 @pytest.mark.parametrize("guess", ["ewma", "rrf"])
 @pytest.mark.parametrize("executor", ["persistent", "streamed"])
 def test_paper_subspace_run_iterations(sw, guess, executor):
-    wl = W.stream_function_2d(kh=2.0, steepness=0.7, dt_tau=1e-4)
+    wl = W.stream_function_2d(kh=2.0, steepness=0.7, dt=DT)
     kw = dict(restart=20, max_restarts=100, tol=1e-8, guess=guess, k=10, decay=0.7, n_init_solves=30)
     if guess == "rrf":
         kw["history"] = 15

@@ -250,12 +250,12 @@ def standing_wave_basin(nx=67, nz=9, depth=1.0, kh=1.0, a_over_h=0.01, steps=128
                 steps=steps, g=G, rho=RHO, m=m, walls=True, relax=None, k=k, omega=float(om))
 
 
-def stream_function_2d(nx=200, nz=20, kh=1.0, steepness=0.6, depth=1.0, steps=200, dt_tau=None):
+def stream_function_2d(nx=200, nz=20, kh=1.0, steepness=0.6, depth=1.0, steps=200, dt=None):
     """Periodic flat-bed slice one wavelength long holding a steady stream-function
     wave (Sec. 5.1): height H = steepness (H/L)_max L with Battjes' limit, crest at
     x = 0, no mean Eulerian current; nx x nz = 200 x 20 as in the paper's study.
-    dt: Courant 0.5 by default; dt_tau gives it in units of sqrt(depth / g) instead
-    (the paper's study steps by 1e-4 in nondimensional time)."""
+    dt: Courant 0.5 by default, else the given step in seconds (the paper's study
+    steps by 1e-4)."""
     from .stream_function import battjes_max_steepness, converged_wave, stream_function_fields
     k = kh / depth
     lx = 2 * math.pi / k
@@ -264,7 +264,7 @@ def stream_function_2d(nx=200, nz=20, kh=1.0, steepness=0.6, depth=1.0, steps=20
     h_over_l = steepness * battjes_max_steepness(kh)
     wave = converged_wave(kh, 2 * math.pi * h_over_l)
     eta, u, w = stream_function_fields(x, depth, nz, wave, k, G)
-    dt = courant_dt(lx / nx, lx, depth) if dt_tau is None else dt_tau * math.sqrt(depth / G)
+    dt = courant_dt(lx / nx, lx, depth) if dt is None else float(dt)
     return dict(name="sfwave2d_%dx%d_kh%g_s%g" % (nx, nz, kh, steepness), nx=nx, ny=1, nz=nz, lx=lx, ly=0.0,
                 h=h, eta=eta, u=u, v=None, w=w, dt=dt, steps=steps, g=G, rho=RHO, m=nx * (nz + 1),
                 kh=kh, steepness=steepness, height=h_over_l * lx, c=wave.c * math.sqrt(G / k), wave=wave)
