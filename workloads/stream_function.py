@@ -178,19 +178,22 @@ class FentonWave:
 
 def converged_wave(kd, kH, tail=1e-10, modes=(32, 48, 64, 96)):
     """The first of the mode counts whose surface series has decayed to `tail`
-    (|E_N| <= tail |E_1|); the shallow steep waves need the most."""
+    (|E_N| <= tail |E_1|); the shallow steep waves need the most.  Raises if
+    none does (a wave too close to breaking for these mode counts)."""
     w = None
     for n in modes:
         w = FentonWave(kd, kH, n_modes=n, start=w)
         if abs(w.E[n]) <= tail * abs(w.E[1]):
             return w
-    return w
+    raise RuntimeError("stream-function series not converged with %d modes (|E_N|/|E_1| = %.1e)"
+                       % (modes[-1], abs(w.E[-1] / w.E[1])))
 
 
 def stream_function_fields(x, h, nz, wave, k, g=G):
     """eta (nx,) about the still level and fixed-frame u, w at every node
     ((nz + 1) * nx, ghost level first) of a flat-bed slice of depth h."""
-    kd = k * h
+    if abs(k * h - wave.kd) > 1e-12 * max(1.0, wave.kd):
+        raise ValueError("the wave was computed for kh = %g, the grid has kh = %g" % (wave.kd, k * h))
     X = k * np.asarray(x, dtype=float)
     eta = wave.surface(X) / k - h
     s = np.arange(-1, nz) / (nz - 1.0)
@@ -198,5 +201,4 @@ def stream_function_fields(x, h, nz, wave, k, g=G):
     Xn = np.broadcast_to(X[None, :], ynode.shape)
     u, w = wave.fixed_frame_velocity(Xn, k * ynode)
     vs = math.sqrt(g / k)
-    assert abs(kd - wave.kd) < 1e-12
     return eta, (u * vs).ravel(), (w * vs).ravel()
