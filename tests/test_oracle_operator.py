@@ -156,3 +156,154 @@ def test_dense_matrix_structure_3d():
     eta = 0.01 * np.cos(np.arange(nx * ny) * 0.7)
     P.assemble(np.zeros(nx * ny), eta)
     assert np.count_nonzero(P.matrix()[r].toarray()) == 91
+
+
+# ---- 3-D: the y-terms of the operator --------------------------------------
+#
+# 4. Still water on a flat bed, periodic x and y: A acting on
+#    cos(kx x + ky y) g(sigma) equals (lambda(kx) + lambda(ky)) g + g''/h^2 with
+#    the two directions' own grid spacings (nx != ny, lx != ly, so a transposed
+#    index or a swapped spacing fails).
+# 5. The 3-D manufactured solution: h, eta^(i-1), eta^(i) and p all vary in x
+#    and y; sympy builds grad^(i) . grad^(i-1) p from the push-forward of
+#    Eq. (9b) with sigma(x, y, z) of Eq. (8), and the ghost row from the bed
+#    normal -(h_x, h_y, 1)/|.|.  Observed order as in 2-D.
+# 6. A problem that varies only in y is the 2-D problem turned by 90 degrees:
+#    the 3-D rows must equal the 2-D oracle's rows along y (same spacing,
+#    same depth profile), value for value.  This reaches every y-coefficient
+#    (sigma_y at both stages, its chi- and sigma-derivatives, the mixed
+#    D_gamma D_sigma term and the ghost row's h_y terms).
+
+def test_flat_still_water_fourier_symbol_3d():
+    nx, ny, nz, lx, ly, H = 16, 12, 9, 2 * math.pi, 3.0, 0.8
+    P = O.OracleProblem(nx, ny, nz, lx, ly, np.full(nx * ny, H))
+    P.assemble()
+    A = P.matrix()
+    x = np.arange(nx) * (lx / nx)
+    y = np.arange(ny) * (ly / ny)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    X, Y = X.ravel(), Y.ravel()
+    s = _sig(nz)
+    dx, dy = lx / nx, ly / ny
+
+    def lam(th, d):
+        return (2 * 2 * math.cos(3 * th) - 27 * 2 * math.cos(2 * th) + 270 * 2 * math.cos(th) - 490) / (180 * d * d)
+
+    for ix_, iy_ in [(0, 1), (1, 0), (2, 3), (5, 4)]:
+        kx, ky = 2 * math.pi * ix_ / lx, 2 * math.pi * iy_ / ly
+        lx_, ly_ = lam(kx * dx, dx), lam(ky * dy, dy)
+        ph = np.cos(kx * X + ky * Y)
+        for q in (0, 2, 5, 6):
+            g = s ** q
+            g1 = q * s ** (q - 1) if q >= 1 else 0 * s
+            g2 = q * (q - 1) * s ** (q - 2) if q >= 2 else 0 * s
+            p = (g[:, None] * ph[None, :]).ravel()
+            yv = (A @ p).reshape(nz + 1, nx * ny)
+            expect = ((lx_ + ly_) * g + g2 / H ** 2)[:, None] * ph[None, :]
+            scale = max(1.0, np.abs(expect).max())
+            np.testing.assert_allclose(yv[1:nz], expect[1:nz], atol=1e-9 * scale)
+            np.testing.assert_allclose(yv[nz], p.reshape(nz + 1, -1)[nz], atol=1e-14)
+            ghost = -(g1[1] / H) * ph
+            np.testing.assert_allclose(yv[0], ghost, atol=1e-9 * max(1.0, abs(ghost).max()))
+
+
+_Y = sp.symbols("Y", real=True)
+_H3 = 1.0 + 0.1 * sp.cos(_X) + 0.08 * sp.sin(_Y) + 0.04 * sp.cos(_X - _Y)
+_E13 = 0.05 * sp.sin(2 * _X) + 0.03 * sp.cos(_Y + 0.2) + 0.02 * sp.sin(_X + _Y)
+_E23 = 0.05 * sp.sin(2 * _X + 0.3) + 0.04 * sp.cos(_Y - 0.4) + 0.02 * sp.cos(_X - 2 * _Y)
+_P3 = sp.cos(_X) * sp.cosh(_S) + _S ** 3 - _S * sp.sin(_X) ** 2 + sp.cos(_Y) * sp.sinh(_S) \
+    + _S ** 2 * sp.sin(_X + 2 * _Y)
+
+
+def _pushforward_coefs_3d(eta):
+    """sigma_x, sigma_y, sigma_z of Eq. (8)-(9b) as functions of (chi, gamma, sigma)."""
+    sig = (_Z + _H3) / (_H3 + eta)
+    zs = _S * (_H3 + eta) - _H3
+    return tuple(sp.diff(sig, v).subs(_Z, zs) for v in (_X, _Y, _Z))
+
+
+_MAN3 = None
+
+
+def _manufactured_3d():
+    sx1, sy1, sz1 = _pushforward_coefs_3d(_E13)
+    sx2, sy2, sz2 = _pushforward_coefs_3d(_E23)
+    # grad^(i-1) p, then grad^(i) . (that field), in (chi, gamma, sigma)
+    V1 = sp.diff(_P3, _X) + sx1 * sp.diff(_P3, _S)
+    V2 = sp.diff(_P3, _Y) + sy1 * sp.diff(_P3, _S)
+    V3 = sz1 * sp.diff(_P3, _S)
+    Lp = (sp.diff(V1, _X) + sx2 * sp.diff(V1, _S) + sp.diff(V2, _Y) + sy2 * sp.diff(V2, _S)
+          + sz2 * sp.diff(V3, _S))
+    hx, hy = sp.diff(_H3, _X), sp.diff(_H3, _Y)
+    nrm = 1 / sp.sqrt(1 + hx ** 2 + hy ** 2)
+    ghost = (-nrm * (hx * V1 + hy * V2 + V3)).subs(_S, 0)
+    args = (_X, _Y, _S)
+    return (sp.lambdify(args, Lp, "numpy"), sp.lambdify((_X, _Y), ghost, "numpy"),
+            [sp.lambdify((_X, _Y), e, "numpy") for e in (_H3, _E13, _E23)], sp.lambdify(args, _P3, "numpy"))
+
+
+def _errors_3d(n, nz):
+    global _MAN3
+    if _MAN3 is None:
+        _MAN3 = _manufactured_3d()
+    f, gfun, (hf, e1f, e2f), pf = _MAN3
+    L = 2 * math.pi
+    x = np.arange(n) * (L / n)
+    X, Yg = np.meshgrid(x, x, indexing="xy")
+    X, Yg = X.ravel(), Yg.ravel()
+    s = _sig(nz)
+    one = np.ones(X.size)
+    P = O.OracleProblem(n, n, nz, L, L, hf(X, Yg) * one)
+    P.assemble(e1f(X, Yg) * one, e2f(X, Yg) * one)
+    p = (pf(X[None, :], Yg[None, :], s[:, None]) * np.ones((nz + 1, 1))).ravel()
+    yv = P.matvec(p).reshape(nz + 1, n * n)
+    exact = f(X[None, :], Yg[None, :], s[:, None]) * np.ones((nz + 1, X.size))
+    err_rows = np.abs(yv - exact).max(axis=1)
+    centred = [j + 1 for j in range(2, nz - 3)]
+    interior = list(range(1, nz))
+    eg = np.abs(yv[0] - gfun(X, Yg) * one).max()
+    return err_rows[centred].max(), err_rows[interior].max(), eg
+
+
+def test_manufactured_convergence_order_3d():
+    res = [_errors_3d(16 * 2 ** q, 8 * 2 ** q + 1) for q in range(3)]
+    e_c = [r[0] for r in res]
+    e_i = [r[1] for r in res]
+    e_g = [r[2] for r in res]
+    ord_c = [math.log2(e_c[q] / e_c[q + 1]) for q in range(2)]
+    ord_i = [math.log2(e_i[q] / e_i[q + 1]) for q in range(2)]
+    ord_g = [math.log2(e_g[q] / e_g[q + 1]) for q in range(2)]
+    assert e_c[-1] < 1e-5 and e_i[-1] < 1e-4, res
+    assert ord_c[-1] > 5.5, (ord_c, res)
+    assert ord_i[-1] > 4.5, (ord_i, res)
+    assert ord_g[-1] > 4.5, (ord_g, res)
+
+
+def test_y_only_problem_is_the_2d_problem_turned():
+    # depth, both surfaces and the unknown vary along y only; nx columns in x are copies
+    nx, ny, nz, L = 8, 24, 9, 2 * math.pi
+    yv = np.arange(ny) * (L / ny)
+    h1 = 1.0 + 0.15 * np.cos(yv) + 0.05 * np.sin(2 * yv)
+    ep1 = 0.04 * np.sin(yv + 0.3)
+    ec1 = 0.04 * np.sin(yv + 0.45) + 0.01 * np.cos(3 * yv)
+    rng = np.random.default_rng(3)
+    p2 = rng.standard_normal((nz + 1, ny))
+    Q = O.OracleProblem(ny, 1, nz, L, 0.0, h1)
+    Q.assemble(ep1, ec1)
+    y2 = Q.matvec(p2.ravel()).reshape(nz + 1, ny)
+    rep = lambda a: np.repeat(a[:, None], nx, axis=1).ravel()     # (iy, ix) layout, x fastest
+    P = O.OracleProblem(nx, ny, nz, L, L, rep(h1))
+    assert P.box
+    P.assemble(rep(ep1), rep(ec1))
+    p3 = np.repeat(p2[:, :, None], nx, axis=2).ravel()
+    y3 = P.matvec(p3).reshape(nz + 1, ny, nx)
+    scale = np.abs(y2).max()
+    for ix in range(nx):
+        np.testing.assert_allclose(y3[:, :, ix], y2, rtol=0, atol=1e-12 * scale)
+    # and the x-only problem is the 2-D problem itself
+    P = O.OracleProblem(ny, nx, nz, L, L, np.tile(h1, nx))
+    P.assemble(np.tile(ep1, nx), np.tile(ec1, nx))
+    p3 = np.repeat(p2[:, None, :], nx, axis=1).ravel()
+    y3 = P.matvec(p3).reshape(nz + 1, nx, ny)
+    for iy in range(nx):
+        np.testing.assert_allclose(y3[:, iy, :], y2, rtol=0, atol=1e-12 * scale)

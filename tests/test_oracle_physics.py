@@ -114,3 +114,61 @@ def test_airy_wave_one_period():
     phase = math.atan2(s1, c1)
     assert abs(amp / 0.01 - 1) < 0.01, amp
     assert abs(phase) / (2 * math.pi) < 0.01, phase
+
+
+# ---- 3-D: the y-components of the stage driver ---------------------------
+
+def test_first_stage_pressure_oblique_wave_3d():
+    # wave vector (1, 2): most of the velocity is along y, so the v terms of
+    # f_eta (Eq. 14b) and of the right-hand side (Eq. 16-17) carry the pressure
+    wl = W.airy_3d(nx=32, ny=32, nz=9, kx_index=1, ky_index=2, a_over_h=0.01)
+    P = O.OracleProblem(wl["nx"], wl["ny"], wl["nz"], wl["lx"], wl["ly"], wl["h"], tol=1e-12, max_restarts=400)
+    st = W.state_arrays(wl)
+    p, stt, code = P.stage((wl["g"], wl["rho"], wl["dt"]), 1, st)
+    assert code == 0, stt
+    x = np.arange(wl["nx"]) * (wl["lx"] / wl["nx"])
+    y = np.arange(wl["ny"]) * (wl["ly"] / wl["ny"])
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    th = (1.0 * X + 2.0 * Y).ravel()
+    k, a, rho, g = math.sqrt(5.0), 0.01, wl["rho"], wl["g"]
+    z = W.node_z(wl["h"], wl["eta"], wl["nz"])
+    plin = -rho * g * z + rho * g * a * np.cosh(k * (z + 1)) / math.cosh(k) * np.cos(th)[None, :]
+    pp = p.reshape(wl["nz"] + 1, -1)
+    dyn = rho * g * a
+    err = np.abs(pp[1:] - plin[1:]).max()
+    assert err < 0.05 * dyn, (err, dyn)
+    # the dynamic part has the wave's shape and size (not just the hydrostatic column)
+    pd = pp[1:] + rho * g * z[1:]
+    corr = np.corrcoef(pd[0], np.cos(th))[0, 1]
+    assert corr > 0.99, corr
+
+
+def test_stage_y_only_equals_2d_stage_turned():
+    # a wave over a bar, both uniform in x and varying along y: every stage of
+    # the 3-D driver must reproduce the 2-D driver (pinned above) run along y,
+    # column by column, with v in the role of u.  The sloping bed reaches the
+    # h_y terms of the ghost rows (operator and right-hand side).
+    ny, nx, nz = 32, 8, 9
+    w2 = W.periodic_bar_2d(nx=ny, nz=nz, kh=1.2, a_over_h=0.02, bar_height=0.4, seed=11)
+    L = w2["lx"]
+    rep = lambda a: np.repeat(np.asarray(a).reshape(-1, ny)[:, :, None], nx, axis=2).ravel()
+    h3 = rep(w2["h"])
+    st2 = W.state_arrays(w2)
+    st3 = dict(u=np.zeros((nz + 1) * ny * nx), v=rep(w2["u"]), w=rep(w2["w"]), eta=rep(w2["eta"]))
+    st3["Ku"], st3["Kv"], st3["Kw"] = (np.zeros_like(st3["u"]) for _ in range(3))
+    st3["Keta"] = np.zeros_like(st3["eta"])
+    phys = (w2["g"], w2["rho"], w2["dt"])
+    kw = dict(tol=1e-13, max_restarts=400, guess="previous")
+    P2 = O.OracleProblem(ny, 1, nz, L, 0.0, w2["h"], **kw)
+    P3 = O.OracleProblem(nx, ny, nz, L, L, h3, **kw)
+    assert P3.box
+    dyn = w2["rho"] * w2["g"] * 0.02
+    for i in range(1, 6):
+        p2, _, c2 = P2.stage(phys, i, st2)
+        p3, _, c3 = P3.stage(phys, i, st3)
+        assert c2 == 0 and c3 == 0
+        np.testing.assert_allclose(p3, rep(p2), rtol=0, atol=1e-9 * dyn)
+        np.testing.assert_allclose(st3["eta"], rep(st2["eta"]), rtol=0, atol=1e-12)
+        np.testing.assert_allclose(st3["v"], rep(st2["u"]), rtol=0, atol=1e-11)
+        np.testing.assert_allclose(st3["w"], rep(st2["w"]), rtol=0, atol=1e-11)
+        assert np.abs(st3["u"]).max() < 1e-12

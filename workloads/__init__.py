@@ -90,6 +90,16 @@ def airy_2d(nx=64, nz=9, kh=1.0, a_over_h=0.01, depth=1.0, steps=50):
     return _wl(nx, 1, nz, lx, 0.0, h, [(k, 0.0, a_over_h * depth, 0.0)], steps, "airy2d_%dx%d" % (nx, nz))
 
 
+def airy_3d(nx=32, ny=32, nz=9, kx_index=1, ky_index=2, a_over_h=0.01, depth=1.0, lx=2 * math.pi,
+            ly=2 * math.pi, steps=50):
+    """Oblique linear Airy wave in a periodic 3-D box over a flat bed; the wave
+    vector (kx, ky) = 2 pi (kx_index / lx, ky_index / ly) lies on the lattice."""
+    kx, ky = 2 * math.pi * kx_index / lx, 2 * math.pi * ky_index / ly
+    h = np.full(nx * ny, depth)
+    return _wl(nx, ny, nz, lx, ly, h, [(kx, ky, a_over_h * depth, 0.0)], steps,
+               "airy3d_%dx%dx%d_k%d_%d" % (nx, ny, nz, kx_index, ky_index))
+
+
 def stokes_like_2d(nx=512, nz=17, kh=2.0, a1_over_h=0.08, depth=1.0, n_harm=4, ratio=0.3, seed=2511,
                    steps=1000):
     """Steep periodic wave: first n_harm harmonics a_n = a1 ratio^(n-1), seeded phases."""
