@@ -229,11 +229,13 @@ int sw_get_last_system(sw_problem *p, double *d_eta_prev, double *d_eta_cur, dou
 
 typedef struct sw_batch sw_batch;
 
-/* Group existing problems (all with the same precision) so that their solves
- * and stages run together: each Poisson solve on one thread block, problems
+/* Group existing two-dimensional problems (all with the same precision; walled
+ * and periodic grids may be mixed) so that their solves and stages run
+ * together: each Poisson solve on one thread block, problems
  * handed out largest first; each driver step one launch over (problem, node).
  * The batch keeps pointers to the problems, which must outlive it.  The
- * many-query setting of Sec. 1 (many wave simulations at once) is the use. */
+ * many-query setting of Sec. 1 (many wave simulations at once) is the use.
+ * SW_ERR_BAD_ARG for a three-dimensional member or mixed precisions. */
 int sw_create_batch(sw_problem *const *problems, int n, sw_batch **out);
 int sw_destroy_batch(sw_batch *b);
 /* Solve every member's system A_i x_i = b_i (Algorithm 2 per member, as

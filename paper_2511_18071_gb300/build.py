@@ -12,7 +12,20 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsawave.so")
-SOURCES = ["setup.cu", "solver.cu", "driver.cu", "batch.cu", "noalloc.cu", "streamed.cu"]
+# (source, object, defines): the persistent solve kernel and the batch kernel
+# are compiled once per variant, so that the variants build in parallel
+_SOLVE = [("f64_p2", "double", "WM_PERIODIC|WM_2D"), ("f64_p3", "double", "WM_PERIODIC|WM_3D"),
+          ("f64_w2", "double", "WM_WALLS|WM_2D"), ("f32_p2", "float", "WM_PERIODIC|WM_2D"),
+          ("f32_p3", "float", "WM_PERIODIC|WM_3D"), ("f32_w2", "float", "WM_WALLS|WM_2D")]
+_BATCH = [("block_f64", "double", 0), ("block_f32", "float", 0), ("cluster_f64", "double", 1),
+          ("cluster_f32", "float", 1)]
+UNITS = ([("batch_kernel.cu", "batch_%s.o" % t, ["-DSW_TI=%s" % ti, "-DSW_CLUSTER=%d" % c,
+                                                  "-DSW_NAME=batch_kernel_%s" % t]) for t, ti, c in _BATCH] +
+         [("solve_kernel.cu", "solve_%s.o" % t, ["-DSW_TI=%s" % ti, "-DSW_WM=(%s)" % wm,
+                                                  "-DSW_NAME=solve_kernel_%s" % t]) for t, ti, wm in _SOLVE] +
+         [(f, f.replace(".cu", ".o"), []) for f in ("streamed.cu", "setup.cu", "solver.cu", "driver.cu", "batch.cu",
+                                                     "noalloc.cu")])
+SOURCES = sorted({u[0] for u in UNITS})
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-Xcompiler", "-pthread", "--expt-relaxed-constexpr"]
@@ -39,18 +52,24 @@ def build(force=False, verbose=False):
     os.makedirs(OUT, exist_ok=True)
     nv = nvcc()
 
-    def comp(src):
-        obj = os.path.join(OUT, src.replace(".cu", ".o"))
-        cmd = [nv] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+    newest = max(os.path.getmtime(d) for d in _deps())
+
+    def comp(unit):
+        src, objname, defs = unit
+        obj = os.path.join(OUT, objname)
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) > newest:
+            return obj
+        cmd = [nv] + ARCH + FLAGS + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError("nvcc failed on %s:\n%s%s" % (src, r.stdout, r.stderr))
+            raise RuntimeError("nvcc failed on %s %s:\n%s%s" % (src, " ".join(defs), r.stdout, r.stderr))
         if verbose:
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(comp, SOURCES))
+    # the slowest units first, all in parallel
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(UNITS), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(comp, UNITS))
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -8,8 +8,8 @@
 #include <numeric>
 #include <utility>
 
+#include "sw_batch.cuh"
 #include "sw_driver.cuh"
-#include "sw_solve.cuh"
 
 namespace sw {
 
@@ -18,59 +18,11 @@ void after_solve(Problem *P, const SolveArgs &A, int guess_only);
 DrvPtrs driver_ptrs(Problem *P);
 int ensure_state(Problem *P);
 
-constexpr size_t BSMEM_FIXED = (sizeof(SmemFixed) + 255) & ~size_t(255);
-
-struct BatchItem {
-    Dev D;
-    SolveArgs A;
-};
 struct DrvItem {
     Dev D;
     DrvPtrs q;
     const double *ep, *ec;
 };
-
-template <typename TI>
-__global__ void __launch_bounds__(NTHREADS, 1) batch_solve_kernel(const BatchItem *items, int n, int *counter) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemFixed &S = *reinterpret_cast<SmemFixed *>(smem_raw);
-    __shared__ int idx;
-    for (;;) {
-        if (threadIdx.x == 0) idx = atomicAdd(counter, 1);
-        __syncthreads();
-        const int i = idx;
-        __syncthreads();
-        if (i >= n) break;
-        const Dev D = items[i].D;
-        const SolveArgs A = items[i].A;
-        BlockTeam tm;
-        solve_body<BlockTeam, TI, 2>(tm, D, A, S, smem_raw + BSMEM_FIXED, nullptr);
-        __syncthreads();
-    }
-}
-
-// The same with one thread-block cluster per member: the cluster's first
-// block takes the next member from the counter and the others read its index
-// through distributed shared memory.  Large members get several SMs.
-template <typename TI>
-__global__ void __launch_bounds__(NTHREADS, 1) batch_solve_cluster_kernel(const BatchItem *items, int n, int *counter) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemFixed &S = *reinterpret_cast<SmemFixed *>(smem_raw);
-    __shared__ int idx;
-    cg::cluster_group cl = cg::this_cluster();
-    for (;;) {
-        if (cl.block_rank() == 0 && threadIdx.x == 0) idx = atomicAdd(counter, 1);
-        cl.sync();
-        const int i = *cl.map_shared_rank(&idx, 0);
-        cl.sync();
-        if (i >= n) break;
-        const Dev D = items[i].D;
-        const SolveArgs A = items[i].A;
-        ClusterTeam tm(S.xchg);
-        solve_body<ClusterTeam, TI, 2>(tm, D, A, S, smem_raw + BSMEM_FIXED, nullptr);
-        cl.sync();
-    }
-}
 
 __global__ void feta_batch(const DrvItem *it) {
     const DrvItem &d = it[blockIdx.y];
@@ -176,9 +128,8 @@ static int upload(Batch *B, cudaStream_t s, bool with_drv, Fill fill) {
     return SW_OK;
 }
 
-static const void *cluster_kern(bool mixed) {
-    return mixed ? (const void *)batch_solve_cluster_kernel<float> : (const void *)batch_solve_cluster_kernel<double>;
-}
+static const void *cluster_kern(bool mixed) { return mixed ? batch_kernel_cluster_f32() : batch_kernel_cluster_f64(); }
+static const void *block_kern(bool mixed) { return mixed ? batch_kernel_block_f32() : batch_kernel_block_f64(); }
 
 // Cluster of cs blocks per member: the largest number of clusters the device
 // can hold at once (0 when it cannot place one).
@@ -225,11 +176,8 @@ static int launch_batch_solve(Batch *B, cudaStream_t s) {
         if (e != cudaSuccess) return cuda_fail(e, "batch cluster launch");
         return SW_OK;
     }
-    if (B->mixed)
-        batch_solve_kernel<float><<<B->nblocks, NTHREADS, B->smem, s>>>(B->d_items, B->n, B->d_counter);
-    else
-        batch_solve_kernel<double><<<B->nblocks, NTHREADS, B->smem, s>>>(B->d_items, B->n, B->d_counter);
-    e = cudaGetLastError();
+    void *args[] = {&B->d_items, &B->n, &B->d_counter};
+    e = cudaLaunchKernel(block_kern(B->mixed), dim3(B->nblocks), dim3(NTHREADS), args, B->smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "batch solve launch");
     return SW_OK;
 }
@@ -253,6 +201,7 @@ extern "C" int sw_create_batch(sw_problem *const *problems, int n, sw_batch **ou
     size_t tiles = 0;
     for (int i = 0; i < n; ++i) {
         Problem *P = (Problem *)problems[B->order[i]];
+        if (P->dev.three_d) { delete B; set_error("a batch holds two-dimensional problems"); return SW_ERR_BAD_ARG; }
         B->probs.push_back(P);
         bool mx = P->params.precision == SW_PRECISION_MIXED;
         if (i == 0) B->mixed = mx;
@@ -263,7 +212,7 @@ extern "C" int sw_create_batch(sw_problem *const *problems, int n, sw_batch **ou
         B->max_m = std::max(B->max_m, P->m);
     }
     B->smem = BSMEM_FIXED + tiles;
-    const void *kern = B->mixed ? (const void *)batch_solve_kernel<float> : (const void *)batch_solve_kernel<double>;
+    const void *kern = block_kern(B->mixed);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem);
     int nsm = 0, per = 0, dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);

@@ -12,25 +12,23 @@
 namespace sw {
 
 // ---------------------------------------------------------------------------
-// Kernels running the solve body of sw_solve.cuh.
+// The persistent solve kernel (solve_kernel.cu), one variant per inner
+// precision and problem class, each compiled on its own.
 // ---------------------------------------------------------------------------
 constexpr size_t SMEM_FIXED = (sizeof(SmemFixed) + 255) & ~size_t(255);
 
-// WALLS selects the instantiation for wall-bounded grids, so the kernel of
-// periodic grids carries none of the wall code (and the other way round).
-template <typename TI, bool WALLS>
-__global__ void __launch_bounds__(NTHREADS, 1) solve_kernel(Dev D, SolveArgs A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemFixed &S = *reinterpret_cast<SmemFixed *>(smem_raw);
-    GridTeam tm(A.part, A.nb);
-    double ph[PH_COUNT];
-    for (int i = 0; i < PH_COUNT; ++i) ph[i] = 0.0;
-    solve_body<GridTeam, TI, WALLS ? 1 : 0>(tm, D, A, S, smem_raw + SMEM_FIXED, ph);
-}
+const void *solve_kernel_f64_p2();   // FP64, periodic, 2-D
+const void *solve_kernel_f64_p3();   // FP64, periodic, 3-D
+const void *solve_kernel_f64_w2();   // FP64, walls (2-D)
+const void *solve_kernel_f32_p2();   // FP32 inner cycles
+const void *solve_kernel_f32_p3();
+const void *solve_kernel_f32_w2();
 
-static const void *solve_kernel_for(bool mixed_precision, bool walls) {
-    if (mixed_precision) return walls ? (const void *)solve_kernel<float, true> : (const void *)solve_kernel<float, false>;
-    return walls ? (const void *)solve_kernel<double, true> : (const void *)solve_kernel<double, false>;
+static const void *solve_kernel_for(const Problem *P) {
+    const bool f32 = P->params.precision == SW_PRECISION_MIXED;
+    if (P->dev.walls) return f32 ? solve_kernel_f32_w2() : solve_kernel_f64_w2();
+    if (P->dev.three_d) return f32 ? solve_kernel_f32_p3() : solve_kernel_f64_p3();
+    return f32 ? solve_kernel_f32_p2() : solve_kernel_f64_p2();
 }
 
 // ---------------------------------------------------------------------------
@@ -136,7 +134,7 @@ int setup_solver_launch(Problem *P) {
     }
     Tiling t = make_tiling(P->dev);
     size_t smem = solve_smem(P->dev, t);
-    const void *kern = solve_kernel_for(mixed(P), P->dev.walls != 0);
+    const void *kern = solve_kernel_for(P);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "solve_kernel smem attribute");
     e = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -245,7 +243,7 @@ static int launch_solve(Problem *P, const double *ep, const double *ec, const do
         int rc = solve_streamed(P, A, s);
         if (rc != SW_OK) return rc;
     } else {
-        const void *kern = solve_kernel_for(mixed(P), P->dev.walls != 0);
+        const void *kern = solve_kernel_for(P);
         e = cudaLaunchCooperativeKernel(kern, P->nblocks, NTHREADS, args, P->smem, s);
         if (e != cudaSuccess) return cuda_fail(e, "solve launch");
         P->launches++;

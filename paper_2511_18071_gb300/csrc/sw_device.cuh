@@ -164,9 +164,10 @@ struct Tiling {
     int TX, TY, HX, HY, HW, ntx, nty, ntiles;
 };
 
-template <typename T, bool WALLS, class Loader, class Store>
+template <typename T, bool WALLS, int TD, class Loader, class Store>
 __device__ inline void apply_tile_t(const Dev &D, const Tiling &tl, int tile, T *sp, T *sq, Loader &ld, Store &st) {
     const int P = D.P, HX = tl.HX, HY = tl.HY, HW = tl.HW;
+    const bool td = TD == 0 ? D.three_d != 0 : TD == 2;
     const int tx0 = (tile % tl.ntx) * tl.TX;
     const int ty0 = (tile / tl.ntx) * tl.TY;
     const int tid = threadIdx.x;
@@ -175,7 +176,7 @@ __device__ inline void apply_tile_t(const Dev &D, const Tiling &tl, int tile, T 
         int l = idx / HW, r = idx - l * HW;
         int a = r % HX, b = r / HX;
         bool hxo = a < HALF || a >= HX - HALF;
-        bool hyo = D.three_d && (b < HALF || b >= HY - HALF);
+        bool hyo = td && (b < HALF || b >= HY - HALF);
         T v = T(0);
         int gx = tx0 + a - HALF;
         if (WALLS) {
@@ -183,7 +184,7 @@ __device__ inline void apply_tile_t(const Dev &D, const Tiling &tl, int tile, T 
             if (gx >= 0 && gx < D.nx) v = ld((long long)l * D.ncol + gx);
         } else if (!(hxo && hyo)) {
             gx = wrapi(gx, D.nx);
-            int gy = D.three_d ? wrapi(ty0 + b - HALF, D.ny) : 0;
+            int gy = td ? wrapi(ty0 + b - HALF, D.ny) : 0;
             v = ld((long long)l * D.ncol + gy * D.nx + gx);
         }
         sp[idx] = v;
@@ -207,8 +208,8 @@ __device__ inline void apply_tile_t(const Dev &D, const Tiling &tl, int tile, T 
     const T *cc = Prec<T>::cc(D);
     for (int idx = tid; idx < P * tl.TX * tl.TY; idx += blockDim.x) {
         int l = idx / (tl.TX * tl.TY), r = idx - l * (tl.TX * tl.TY);
-        int a = r % tl.TX + HALF, b = D.three_d ? r / tl.TX + HALF : 0;
-        int gx = tx0 + a - HALF, gy = D.three_d ? ty0 + b - HALF : 0;
+        int a = r % tl.TX + HALF, b = td ? r / tl.TX + HALF : 0;
+        int gx = tx0 + a - HALF, gy = td ? ty0 + b - HALF : 0;
         int c = gy * D.nx + gx;
         int hr = b * HX + a;
         long long node = (long long)l * n + c;
@@ -245,10 +246,10 @@ __device__ inline void apply_tile_t(const Dev &D, const Tiling &tl, int tile, T 
 #pragma unroll
             for (int t = -HALF; t <= HALF; ++t) {
                 px += wa1[t + HALF] * sp[HW + hr + x0 + HALF + t];
-                if (D.three_d) py += wy1[t + HALF] * sp[HW + hr + t * HX];
+                if (td) py += wy1[t + HALF] * sp[HW + hr + t * HX];
             }
             y = cc[CC_GS * n + c] * sq[HW + hr] + cc[CC_GX * n + c] * px;
-            if (D.three_d) y += cc[CC_GY * n + c] * py;
+            if (td) y += cc[CC_GY * n + c] * py;
         } else {
             T sg = T(l - 1) * inv_nzm1;
             T ap1 = cc[CC_AP1 * n + c];
@@ -272,7 +273,7 @@ __device__ inline void apply_tile_t(const Dev &D, const Tiling &tl, int tile, T 
 #pragma unroll
             for (int k = 0; k < W; ++k) pss += w2[k] * pc[k * HW];
             y = pxx + c_xs * pxs + c_s * ql[0];
-            if (D.three_d) {
+            if (td) {
                 T ay1 = cc[CC_AY1 * n + c];
                 T ay = cc[CC_AY0 * n + c] - sg * ay1;
                 T by = cc[CC_BY0 * n + c] - sg * cc[CC_BY1 * n + c];
@@ -295,16 +296,21 @@ __device__ inline void apply_tile_t(const Dev &D, const Tiling &tl, int tile, T 
     __syncthreads();
 }
 
-// Wall mode of a caller: 0 periodic grids only, 1 walls only (both fixed at
-// compile time, so a kernel instantiated for one kind carries no code for the
-// other), 2 decided per problem at run time (batches mixing both).
+// Problem class a kernel is compiled for (its "mode" WM), so that a kernel
+// instantiated for one class carries no code for the others:
+//   bits 0-1, walls: 0 periodic grids only, 1 walls only, 2 decided per problem
+//            at run time (batches mixing both);
+//   bits 2-3, dimension: 0 decided per problem, 1 two-dimensional only (the
+//            CROSS2D and BOX2D preconditioner layouts), 2 three-dimensional only.
+constexpr int WM_PERIODIC = 0, WM_WALLS = 1, WM_ANYWALL = 2, WM_2D = 4, WM_3D = 8;
 template <int WM>
-__device__ __forceinline__ bool walls_of(const Dev &D) { return WM == 2 ? D.walls != 0 : WM == 1; }
+__device__ __forceinline__ bool walls_of(const Dev &D) { return (WM & 3) == 2 ? D.walls != 0 : (WM & 3) == 1; }
+template <int WM> constexpr int dim_of() { return (WM >> 2) & 3; }
 
 template <typename T, int WM = 2, class Loader, class Store>
 __device__ inline void apply_tile(const Dev &D, const Tiling &tl, int tile, T *sp, T *sq, Loader &ld, Store &st) {
-    if (walls_of<WM>(D)) apply_tile_t<T, true>(D, tl, tile, sp, sq, ld, st);
-    else apply_tile_t<T, false>(D, tl, tile, sp, sq, ld, st);
+    if (walls_of<WM>(D)) apply_tile_t<T, true, 1>(D, tl, tile, sp, sq, ld, st);
+    else apply_tile_t<T, false, dim_of<WM>()>(D, tl, tile, sp, sq, ld, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -627,11 +633,13 @@ __device__ inline void ilu_gather_row(const Dev &D, int c, long long row, const 
         else ilu_gather_row_t<BOX2D, T, TI, LOWER, true>(D, c, row, in, out);
         return;
     }
-    switch (D.layout) {
-    case CROSS2D: ilu_gather_row_t<CROSS2D, T, TI, LOWER, false>(D, c, row, in, out); break;
-    case BOX2D: ilu_gather_row_t<BOX2D, T, TI, LOWER, false>(D, c, row, in, out); break;
-    case CROSS3D: ilu_gather_row_t<CROSS3D, T, TI, LOWER, false>(D, c, row, in, out); break;
-    default: ilu_gather_row_t<BOX3D, T, TI, LOWER, false>(D, c, row, in, out); break;
+    if constexpr (dim_of<WM>() != 2) {
+        if (D.layout == CROSS2D) { ilu_gather_row_t<CROSS2D, T, TI, LOWER, false>(D, c, row, in, out); return; }
+        if (D.layout == BOX2D) { ilu_gather_row_t<BOX2D, T, TI, LOWER, false>(D, c, row, in, out); return; }
+    }
+    if constexpr (dim_of<WM>() != 1) {
+        if (D.layout == CROSS3D) ilu_gather_row_t<CROSS3D, T, TI, LOWER, false>(D, c, row, in, out);
+        else ilu_gather_row_t<BOX3D, T, TI, LOWER, false>(D, c, row, in, out);
     }
 }
 template <typename T, int WM = 2>
@@ -659,11 +667,13 @@ __device__ inline void ilu_fwd_column(const Dev &D, int c, int q, const TI *in, 
         else ilu_fwd_column_t<BOX2D, T, TI, true>(D, c, q, in, out, lane);
         return;
     }
-    switch (D.layout) {
-    case CROSS2D: ilu_fwd_column_t<CROSS2D, T, TI, false>(D, c, q, in, out, lane); break;
-    case BOX2D: ilu_fwd_column_t<BOX2D, T, TI, false>(D, c, q, in, out, lane); break;
-    case CROSS3D: ilu_fwd_column_t<CROSS3D, T, TI, false>(D, c, q, in, out, lane); break;
-    default: ilu_fwd_column_t<BOX3D, T, TI, false>(D, c, q, in, out, lane); break;
+    if constexpr (dim_of<WM>() != 2) {
+        if (D.layout == CROSS2D) { ilu_fwd_column_t<CROSS2D, T, TI, false>(D, c, q, in, out, lane); return; }
+        if (D.layout == BOX2D) { ilu_fwd_column_t<BOX2D, T, TI, false>(D, c, q, in, out, lane); return; }
+    }
+    if constexpr (dim_of<WM>() != 1) {
+        if (D.layout == CROSS3D) ilu_fwd_column_t<CROSS3D, T, TI, false>(D, c, q, in, out, lane);
+        else ilu_fwd_column_t<BOX3D, T, TI, false>(D, c, q, in, out, lane);
     }
 }
 template <typename T, int WM = 2>
@@ -673,11 +683,13 @@ __device__ inline void ilu_bwd_column(const Dev &D, int c, int q, T *out, int la
         else ilu_bwd_column_t<BOX2D, T, true>(D, c, q, out, lane);
         return;
     }
-    switch (D.layout) {
-    case CROSS2D: ilu_bwd_column_t<CROSS2D, T, false>(D, c, q, out, lane); break;
-    case BOX2D: ilu_bwd_column_t<BOX2D, T, false>(D, c, q, out, lane); break;
-    case CROSS3D: ilu_bwd_column_t<CROSS3D, T, false>(D, c, q, out, lane); break;
-    default: ilu_bwd_column_t<BOX3D, T, false>(D, c, q, out, lane); break;
+    if constexpr (dim_of<WM>() != 2) {
+        if (D.layout == CROSS2D) { ilu_bwd_column_t<CROSS2D, T, false>(D, c, q, out, lane); return; }
+        if (D.layout == BOX2D) { ilu_bwd_column_t<BOX2D, T, false>(D, c, q, out, lane); return; }
+    }
+    if constexpr (dim_of<WM>() != 1) {
+        if (D.layout == CROSS3D) ilu_bwd_column_t<CROSS3D, T, false>(D, c, q, out, lane);
+        else ilu_bwd_column_t<BOX3D, T, false>(D, c, q, out, lane);
     }
 }
 

@@ -251,7 +251,7 @@ __device__ inline void team_ilu(Team &tm, const Dev &D, const TIn *in, TI *out) 
     // their FP64 pipes and load units
     const int gw = (threadIdx.x >> 5) * tm.nb + tm.bid;
     const int nw = tm.nb * NWARPS;
-    const int ng = WM == 0 ? 4 : D.ngroups;   // periodic grids: the four colours
+    const int ng = (WM & 3) == 0 ? 4 : D.ngroups;   // periodic grids: the four colours
     if (group_size<WM>(D, 0) > 4 * nw) {
         // large problem: row-parallel coupling gathers, then per-column products
         const long long tid = (long long)tm.bid * NTHREADS + threadIdx.x, nth = (long long)tm.nb * NTHREADS;
