@@ -97,6 +97,10 @@ typedef struct {
     uint64_t seed;      /* seed of the Gaussian sketch vectors omega */
     int executor;       /* SW_EXEC_*: how a solve is run on the GPU (same arithmetic) */
     int history;        /* K of the range finder: solutions kept, k..SW_RRF_MAX_HISTORY (SW_GUESS_RRF) */
+    int orthonormalize; /* 1: the guess uses V = Q, an orthonormal basis of the sketch's span (the optional
+                           QR step of Algorithms 3 and 4), by CholeskyQR2 with columns below the rank guard
+                           dropped; 0: V = Y.  Same x0 in exact arithmetic; costs three passes over the
+                           sketch and a k x m buffer */
 } sw_params;
 
 typedef struct {

@@ -45,7 +45,7 @@ class Relaxation(C.Structure):
 class Params(C.Structure):
     _fields_ = [("restart", C.c_int), ("max_restarts", C.c_int), ("tol", C.c_double), ("guess", C.c_int),
                 ("k", C.c_int), ("decay", C.c_double), ("n_init_solves", C.c_int), ("precision", C.c_int),
-                ("seed", C.c_uint64), ("executor", C.c_int), ("history", C.c_int)]
+                ("seed", C.c_uint64), ("executor", C.c_int), ("history", C.c_int), ("orthonormalize", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -343,10 +343,10 @@ class Problem:
 
     def __init__(self, nx, ny, nz, lx, ly, h, restart=20, max_restarts=50, tol=1e-8, guess="cold", k=10,
                  decay=0.9, n_init_solves=30, precision="fp64", seed=2511, walls=False, executor="auto",
-                 history=15):
+                 history=15, orthonormalize=False):
         self.grid = Grid(nx, ny, nz, lx, ly if ny > 1 else 0.0, int(bool(walls)))
         self.params = Params(restart, max_restarts, tol, GUESS[guess], k, decay, n_init_solves,
-                             PRECISION[precision], seed, EXECUTOR[executor], history)
+                             PRECISION[precision], seed, EXECUTOR[executor], history, int(bool(orthonormalize)))
         self.handle = create_problem(self.grid, self.params, h)
         self.m = problem_size(self.handle)
         self.ncol = nx * ny

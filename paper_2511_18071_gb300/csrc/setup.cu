@@ -411,6 +411,10 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
         set_error("grid: walls need a 2-D grid with nx >= 16");
         return SW_ERR_BAD_ARG;
     }
+    if (p.orthonormalize != 0 && p.orthonormalize != 1) {
+        set_error("params: orthonormalize must be 0 or 1");
+        return SW_ERR_BAD_ARG;
+    }
     if (p.guess == SW_GUESS_RRF && (p.history < p.k || p.history > SW_RRF_MAX_HISTORY)) {
         set_error("params: the range finder needs k <= history <= 16");
         return SW_ERR_BAD_ARG;
@@ -584,6 +588,7 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     ALLOC(P->d_W, (size_t)p.k * m * sizeof(double));
     ALLOC(P->d_xprev, (size_t)m * sizeof(double));
     if (p.guess == SW_GUESS_RRF) ALLOC(P->d_X, (size_t)p.history * m * sizeof(double));
+    if (p.orthonormalize) ALLOC(P->d_Q, (size_t)p.k * m * sizeof(double));
     ALLOC(P->d_omega, MAX_K * sizeof(double));
     ALLOC(P->d_stats, sizeof(DevStats));
     ALLOC(P->d_host_io, (3 * (size_t)m + 2 * (size_t)H.ncol) * sizeof(double));

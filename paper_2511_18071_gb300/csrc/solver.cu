@@ -180,6 +180,7 @@ SolveArgs make_args(Problem *P, const double *ep, const double *ec, const double
     A.r = P->d_work; A.t = (void *)(P->d_work + P->m);
     A.Yold = P->d_Y[P->ybuf]; A.Ynew = P->d_Y[P->ybuf ^ 1];
     A.Wm = P->d_W; A.xprev = P->d_xprev; A.part = P->d_part; A.stats = (DevStats *)P->d_stats;
+    A.Vq = P->params.orthonormalize ? P->d_Q : nullptr;
     A.tl = tiling_of(P);
     A.restart = pr.restart; A.max_restarts = pr.max_restarts; A.k = pr.k; A.nb = P->nblocks;
     A.tol = pr.tol; A.decay = pr.decay; A.guess_only = guess_only;

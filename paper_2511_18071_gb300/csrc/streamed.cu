@@ -263,6 +263,30 @@ __global__ void __launch_bounds__(NTHREADS) sk_gram(const double *Wm, const doub
     }
 }
 
+// V = Y R^-1 with R from CholeskyQR2 of the sketch (the optional QR step of
+// Algorithms 3 and 4), or V = Y when its Gram matrix could not be factored
+__global__ void __launch_bounds__(NTHREADS) sk_orth_v(const double *Y, const SState *ss, int k, double *Vq,
+                                                       long long m) {
+    __shared__ double R[MAX_K * MAX_K];
+    for (int i = threadIdx.x; i < k * k; i += blockDim.x) R[i] = ss->R[i];
+    __syncthreads();
+    const bool ok = ss->chol_ok != 0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += (long long)gridDim.x * blockDim.x) {
+        double q[MAX_K];
+#pragma unroll
+        for (int c = 0; c < MAX_K; ++c) {
+            if (c >= k) break;
+            double sv = Y[(size_t)c * m + p];
+            if (ok) {
+                for (int i = 0; i < c; ++i) sv -= q[i] * R[i * k + c];
+                sv /= R[c * k + c];
+            }
+            q[c] = sv;
+            Vq[(size_t)c * m + p] = sv;
+        }
+    }
+}
+
 // x0 = Y z (EWMA), x_prev (previous solution) or 0 (cold start)
 __global__ void __launch_bounds__(NTHREADS) sk_x0(const double *Y, const double *xprev, const SState *ss, int k,
                                                    int mode, double *x, long long m) {
@@ -450,13 +474,13 @@ __global__ void sk_ctl_bnorm(const double *part, int nb, SState *ss, CtlArgs c) 
 }
 
 // a9, step 1: G = W^T W, c1 = W^T b, Cholesky (shifted when not numerically SPD)
-__global__ void sk_ctl_chol1(const double *part, int nb, SState *ss, CtlArgs c, long long m, int upd) {
+__global__ void sk_ctl_chol1(const double *part, int nb, SState *ss, CtlArgs c, long long m, int upd, int w_cost) {
     __shared__ double res[PART_STRIDE];
     const int k = c.k, ng = k * (k + 1) / 2, nv = ng + k;
     reduce_parts(part, nv, nb, res);
     if (threadIdx.x == 0) {
         if (upd) add_cost(ss, c, 3.0 * k, (2.0 * k + 1.0) * 8.0);
-        add_cost(ss, c, k * c.cm.fA, k * (c.cm.bA + 8.0));
+        if (w_cost) add_cost(ss, c, k * c.cm.fA, k * (c.cm.bA + 8.0));
         add_cost(ss, c, 2.0 * nv, (k + 1.0) * 8.0);
     }
     if (threadIdx.x < 32) {
@@ -922,15 +946,18 @@ static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
             rc.newest = A.ring_newest;
             double *Ync = A.Ynew + (size_t)cc * m;
             sk_rrf_y<<<SNB, NTHREADS, 0, s>>>(A.ring, rc, Ync, m);
-            sk_apply_w<WM><<<tl.ntiles, NTHREADS, smD, s>>>(D, tl, Ync, A.xprev, 0.0, 0.0, 0, A.Wm + (size_t)cc * m);
-            launches += 2;
+            ++launches;
+            if (!A.Vq) {
+                sk_apply_w<WM><<<tl.ntiles, NTHREADS, smD, s>>>(D, tl, Ync, A.xprev, 0.0, 0.0, 0, A.Wm + (size_t)cc * m);
+                ++launches;
+            }
         }
     } else if (upd || A.guess_mode == SW_GUESS_EWMA) {
         for (int cc = 0; cc < k; ++cc) {
             const double *Yc = A.Yold + (size_t)cc * m;
             double *Ync = A.Ynew + (size_t)cc * m;
             if (upd) { sk_ynew<<<SNB, NTHREADS, 0, s>>>(Yc, A.xprev, A.decay, A.omega[cc], Ync, m); ++launches; }
-            if (A.guess_mode == SW_GUESS_EWMA) {
+            if (A.guess_mode == SW_GUESS_EWMA && !A.Vq) {
                 sk_apply_w<WM><<<tl.ntiles, NTHREADS, smD, s>>>(D, tl, Yc, A.xprev, A.decay, A.omega[cc], upd,
                                                                  A.Wm + (size_t)cc * m);
                 ++launches;
@@ -938,9 +965,23 @@ static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
         }
     }
     const double *Ycur = (A.pending || A.guess_mode == SW_GUESS_RRF) ? A.Ynew : A.Yold;
+    const bool orth = A.Vq && (A.guess_mode == SW_GUESS_EWMA || A.guess_mode == SW_GUESS_RRF);
+    if (orth) {
+        // the optional QR step of Algorithms 3 and 4: CholeskyQR2 of Y, V = Y R^-1, then W = A V
+        sk_gram<<<SNB, NTHREADS, 0, s>>>(Ycur, A.b, m, k, ss, 0, S->partB);
+        sk_ctl_chol1<<<1, NTHREADS, 0, s>>>(S->partB, SNB, ss, c, m, upd, 1);
+        sk_gram<<<SNB, NTHREADS, 0, s>>>(Ycur, A.b, m, k, ss, 1, S->partB);
+        sk_ctl_chol2<<<1, NTHREADS, 0, s>>>(S->partB, SNB, ss, c);
+        sk_orth_v<<<SNB, NTHREADS, 0, s>>>(Ycur, ss, k, A.Vq, m);
+        for (int cc = 0; cc < k; ++cc)
+            sk_apply_w<WM><<<tl.ntiles, NTHREADS, smD, s>>>(D, tl, A.Vq + (size_t)cc * m, A.xprev, 0.0, 0.0, 0,
+                                                             A.Wm + (size_t)cc * m);
+        launches += 5 + k;
+        Ycur = A.Vq;
+    }
     if (A.guess_mode == SW_GUESS_EWMA || A.guess_mode == SW_GUESS_RRF) {
         sk_gram<<<SNB, NTHREADS, 0, s>>>(A.Wm, A.b, m, k, ss, 0, S->partB);
-        sk_ctl_chol1<<<1, NTHREADS, 0, s>>>(S->partB, SNB, ss, c, m, upd);
+        sk_ctl_chol1<<<1, NTHREADS, 0, s>>>(S->partB, SNB, ss, c, m, orth ? 0 : upd, orth ? 0 : 1);
         sk_gram<<<SNB, NTHREADS, 0, s>>>(A.Wm, A.b, m, k, ss, 1, S->partB);
         sk_ctl_chol2<<<1, NTHREADS, 0, s>>>(S->partB, SNB, ss, c);
         launches += 4;

@@ -109,6 +109,7 @@ struct Problem {
     double *d_W = nullptr;         // k x m, A Y
     double *d_xprev = nullptr;
     double *d_X = nullptr;         // range finder: history x m past solutions
+    double *d_Q = nullptr;         // k x m orthonormal basis of the sketch (orthonormalize)
     double *d_part = nullptr;      // per-block partial sums
     double *d_omega = nullptr;     // k doubles
     void *d_stats = nullptr;       // DevStats

@@ -42,6 +42,8 @@ struct SolveArgs {
     double *ring_store;       // slot that receives this solve's solution (null: none)
     int ring_K, ring_Ke, ring_newest;   // slots, solutions used, slot of the newest
     double omega_rrf[SW_RRF_MAX_HISTORY * MAX_K];   // row r (r-th newest) x column c at r k + c
+    // optional V = Q of the sketch (the QR step of Algorithms 3 and 4)
+    double *Vq;               // k x m, null unless orthonormalize
 };
 
 // Phases of a solve, timed between barriers by the team's first thread (profiling aid).
@@ -403,7 +405,7 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
     if (A.guess_mode == SW_GUESS_RRF) {
         // Algorithm 3: Y = X Omega over the newest solutions, then W = A Y (FP64)
         cost(2.0 * A.ring_Ke * k, (A.ring_Ke + k) * 8.0);
-        cost(k * A.cm.fA, k * (A.cm.bA + 8.0));
+        if (!A.Vq) cost(k * A.cm.fA, k * (A.cm.bA + 8.0));
         for (int c = 0; c < k; ++c) {
             double *Ync = Ynew + (size_t)c * m;
             for (long long p = tid; p < m; p += nth) {
@@ -416,23 +418,25 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
             }
         }
         tm.sync();
-        for (int c = 0; c < k; ++c) {
-            StVec<double, double> st{Wm + (size_t)c * m};
-            LdVec<double, double> ld{Ynew + (size_t)c * m, 1.0};
-            team_apply<Team, double, WM>(tm, D, A.tl, tiles, ld, st);
+        if (!A.Vq) {
+            for (int c = 0; c < k; ++c) {
+                StVec<double, double> st{Wm + (size_t)c * m};
+                LdVec<double, double> ld{Ynew + (size_t)c * m, 1.0};
+                team_apply<Team, double, WM>(tm, D, A.tl, tiles, ld, st);
+            }
+            tm.sync();
         }
-        tm.sync();
     } else if (A.pending || A.guess_mode == SW_GUESS_EWMA) {
         // Y_new = r Y_old + x_prev omega^T (Algorithm 4) and W = A Y_new
         const bool upd = A.pending != 0;
         if (upd) cost(3.0 * k, (2.0 * k + 1.0) * 8.0);
-        if (A.guess_mode == SW_GUESS_EWMA) cost(k * A.cm.fA, k * (A.cm.bA + 8.0));
+        if (A.guess_mode == SW_GUESS_EWMA && !A.Vq) cost(k * A.cm.fA, k * (A.cm.bA + 8.0));
         for (int c = 0; c < k; ++c) {
             const double *Yc = Yold + (size_t)c * m;
             double *Ync = Ynew + (size_t)c * m;
             if (upd)
                 for (long long p = tid; p < m; p += nth) Ync[p] = A.decay * Yc[p] + A.omega[c] * A.xprev[p];
-            if (A.guess_mode == SW_GUESS_EWMA) {
+            if (A.guess_mode == SW_GUESS_EWMA && !A.Vq) {
                 // W = A Y in FP64 (the least squares needs it accurate)
                 StVec<double, double> st{Wm + (size_t)c * m};
                 if (upd) {
@@ -446,8 +450,96 @@ __device__ void solve_body(Team &tm, const Dev &D, const SolveArgs &A, SmemFixed
         }
         tm.sync();
     }
-    tick(PH_GUESS_W);
     const double *Ycur = (A.pending || A.guess_mode == SW_GUESS_RRF) ? Ynew : Yold;
+    if (A.Vq && (A.guess_mode == SW_GUESS_EWMA || A.guess_mode == SW_GUESS_RRF)) {
+        // the optional QR step of Algorithms 3 and 4: V = Y R^-1 with R from CholeskyQR2 of Y
+        // (shifted Cholesky when Y^T Y is not numerically SPD), then W = A V
+        const int ng = k * (k + 1) / 2;
+        cost(2.0 * ng + (double)k * k + 2.0 * ng + (double)k * k, 3.0 * k * 8.0 + k * 8.0);
+        cost(k * A.cm.fA, k * (A.cm.bA + 8.0));
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1 && !S.flags[0]) break;
+            tm.sum_many(ng, S, S.res, [&](int c0, double (&v)[32]) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = 0.0;
+                for (long long p = tid; p < m; p += nth) {
+                    double q[MAX_K];
+#pragma unroll
+                    for (int c = 0; c < MAX_K; ++c) {
+                        if (c >= k) { q[c] = 0.0; continue; }
+                        double sv = Ycur[(size_t)c * m + p];
+                        if (pass == 1) {
+                            for (int i = 0; i < c; ++i) sv -= q[i] * S.R1[i * k + c];
+                            sv /= S.R1[c * k + c];
+                        }
+                        q[c] = sv;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int e = c0 + i;
+                        if (e >= ng) break;
+                        v[i] += q[S.ga[e]] * q[S.gb[e]];
+                    }
+                }
+            });
+            if (threadIdx.x < 32) {
+                for (int e = threadIdx.x; e < ng; e += 32) {
+                    S.G[S.ga[e] * k + S.gb[e]] = S.res[e];
+                    S.G[S.gb[e] * k + S.ga[e]] = S.res[e];
+                }
+                __syncwarp();
+                if (pass == 0) {
+                    double tr = 0.0;
+                    for (int c = 0; c < k; ++c) tr += S.G[c * k + c];
+                    for (int i = threadIdx.x; i < k * k; i += 32) S.R[i] = S.G[i];
+                    __syncwarp();
+                    bool ok = tr > 0.0 && warp_cholesky(S.G, S.R1, k);
+                    if (!ok && tr > 0.0) {
+                        double sh = 11.0 * ((double)m * k + (double)k * (k + 1)) * 1.1102230246251565e-16 * tr;
+                        for (int i = threadIdx.x; i < k * k; i += 32) S.G[i] = S.R[i] + ((i / k == i % k) ? sh : 0.0);
+                        __syncwarp();
+                        ok = warp_cholesky(S.G, S.R1, k);
+                    }
+                    // R = R1 unless the second pass refines it
+                    for (int i = threadIdx.x; i < k * k; i += 32) S.R[i] = S.R1[i];
+                    if (threadIdx.x == 0) S.flags[0] = ok ? 1 : 0;
+                } else if (warp_cholesky(S.G, S.R2, k)) {
+                    for (int e = threadIdx.x; e < k * k; e += 32) {
+                        int a = e / k, bc = e % k;
+                        double sv = 0.0;
+                        for (int l = a; l <= bc; ++l) sv += S.R2[a * k + l] * S.R1[l * k + bc];
+                        S.R[e] = bc >= a ? sv : 0.0;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // V = Y R^-1, or V = Y when the Gram matrix is zero or not factorable
+        const bool ok = S.flags[0] != 0;
+        for (long long p = tid; p < m; p += nth) {
+            double q[MAX_K];
+#pragma unroll
+            for (int c = 0; c < MAX_K; ++c) {
+                if (c >= k) break;
+                double sv = Ycur[(size_t)c * m + p];
+                if (ok) {
+                    for (int i = 0; i < c; ++i) sv -= q[i] * S.R[i * k + c];
+                    sv /= S.R[c * k + c];
+                }
+                q[c] = sv;
+                A.Vq[(size_t)c * m + p] = sv;
+            }
+        }
+        tm.sync();
+        for (int c = 0; c < k; ++c) {
+            StVec<double, double> st{Wm + (size_t)c * m};
+            LdVec<double, double> ld{A.Vq + (size_t)c * m, 1.0};
+            team_apply<Team, double, WM>(tm, D, A.tl, tiles, ld, st);
+        }
+        tm.sync();
+        Ycur = A.Vq;
+    }
+    tick(PH_GUESS_W);
     if (A.guess_mode == SW_GUESS_EWMA || A.guess_mode == SW_GUESS_RRF) {
         // Gram G = W^T W and c = W^T b (a8)
         const int ng = k * (k + 1) / 2;

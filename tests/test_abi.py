@@ -66,6 +66,7 @@ def test_new_parameters_rejected_on_host(sw):
         sw.Params(20, 5, 1e-8, 3, 4, 0.9, 0, 0, 1, 0, 17),    # range finder: history above 16
         sw.Params(20, 5, 1e-8, 4, 4, 0.9, 0, 0, 1, 0, 15),    # unknown guess
         sw.Params(20, 5, 1e-8, 2, 4, 0.9, 0, 0, 1, 7, 15),    # unknown executor
+        sw.Params(20, 5, 1e-8, 2, 4, 0.9, 0, 0, 1, 0, 15, 2),  # orthonormalize is 0 or 1
     ]
     for p in bad:
         with pytest.raises(sw.SawaveError) as e:

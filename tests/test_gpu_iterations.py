@@ -1,0 +1,128 @@
+"""GPU iteration counts against the oracle, solve by solve.
+
+1. Config 1 (64 x 9 linear Airy wave, GMRES(20), tol 1e-8, EWMA k = 10,
+   r = 0.9, six steps of previous-solution warm-up) over its full 50 steps:
+   the GPU solves the 250 systems of the oracle's own run, keeping its own
+   sketch, and each solve's iteration count equals the oracle's within +-1
+   (a residual landing within rounding of the threshold may stop one step
+   earlier on either side), with at most a fifth of them off by one.
+2. The 512 x 17 steep wave (the benchmark's workload and configuration):
+   before each of 30 EWMA solves of the GPU's own trajectory, the GPU's sketch
+   (the one its next guess uses) and, after the solve, its system are handed
+   to the oracle, which forms its own guess (Householder QR) and runs its own
+   GMRES from it.  Given identical inputs, the guesses' residuals agree to
+   1e-6 relative (the device's CholeskyQR2 and the oracle's QR differ only by
+   rounding on these sketches, condition ~1e6) and the counts agree to +-1.
+   Counts along two independent trajectories are not compared here: they
+   diverge with the rounding of the stage driver (the oracle against itself
+   under perturbations of 1e-13: tests/test_sensitivity.py).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def sw():
+    from paper_2511_18071_gb300 import build
+    build.build()
+    import paper_2511_18071_gb300 as sw
+    assert torch.cuda.is_available()
+    return sw
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
+
+
+def _record(wl, nsteps, **kw):
+    """Systems (eta_prev, eta_cur, b) and iteration counts of an oracle run of the stage driver."""
+    ora = O.OracleProblem(wl["nx"], wl["ny"], wl["nz"], wl["lx"], wl["ly"], wl["h"], **kw)
+    st = W.state_arrays(wl)
+    phys = (wl["g"], wl["rho"], wl["dt"])
+    al, be, _ = O.lserk45()
+    out = []
+    for _ in range(nsteps):
+        for i in range(1, 6):
+            feta = ora.f_eta(st["u"], st["v"], st["w"], st["eta"])
+            keta = al[i - 1] * st["Keta"] + wl["dt"] * feta
+            eta_new = st["eta"] + be[i - 1] * keta
+            b = ora.rhs(phys, i, st["u"], st["v"], st["w"], st["Ku"], st["Kv"], st["Kw"], st["eta"], eta_new, feta)
+            eprev = st["eta"].copy()
+            p, s, code = ora.stage(phys, i, st)
+            assert code == 0
+            out.append((eprev, eta_new.copy(), b, p, s))
+    return out
+
+
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_config1_fifty_steps_iterations(sw, executor):
+    wl = W.airy_2d(nx=64, nz=9, kh=1.0, a_over_h=0.01, steps=50)
+    kw = dict(restart=20, max_restarts=100, tol=1e-8, guess="ewma", k=10, decay=0.9, n_init_solves=30)
+    rec = _record(wl, 50, **kw)
+    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], executor=executor, **kw)
+    x = torch.zeros(gpu.m, dtype=torch.float64, device=DEV)
+    diffs, its = [], []
+    for ep, ec, b, p, so in rec:
+        gpu.solve(_t(ep), _t(ec), _t(b), x)
+        sg = gpu.stats()
+        assert sg["status"] == 0, sg
+        diffs.append(sg["iterations"] - so["iterations"])
+        its.append(so["iterations"])
+        err = np.linalg.norm(x.cpu().numpy() - p) / np.linalg.norm(p)
+        assert err < 1e-6, err          # both meet 1e-8 on the preconditioned residual
+    gpu.close()
+    diffs = np.array(diffs)
+    assert len(diffs) == 250
+    assert np.all(np.abs(diffs) <= 1), diffs
+    assert np.count_nonzero(diffs) <= len(diffs) // 5, diffs
+    # the subspace guess is doing the work: far fewer iterations than the warm-up solves
+    assert np.mean(its[30:]) < 0.5 * np.mean(its[5:30]), its
+
+
+def test_headline_shared_sketch_and_system(sw):
+    wl = W.stokes_like_2d(nx=512, nz=17, kh=2.0, a1_over_h=0.08, steps=1000)
+    k = 10
+    kw = dict(restart=20, max_restarts=500, tol=1e-8, guess="ewma", k=k, decay=0.9, n_init_solves=30, seed=2511)
+    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], executor="auto", **kw)
+    sw.set_physics(gpu.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+    sw.set_state(gpu.handle, _t(wl["u"]), None, _t(wl["w"]), _t(wl["eta"]))
+    ora = O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw)
+    m = gpu.m
+    Y = torch.empty(k * m, dtype=torch.float64, device=DEV)
+    ep = torch.empty(gpu.ncol, dtype=torch.float64, device=DEV)
+    ec = torch.empty_like(ep)
+    b = torch.empty(m, dtype=torch.float64, device=DEV)
+    rows = []
+    for q in range(60):
+        if q >= 30:
+            sw.get_sketch(gpu.handle, Y)
+        sw.advance_stage(gpu.handle)
+        sg = gpu.stats()
+        assert sg["status"] == 0, sg
+        if q < 30:
+            continue
+        sw.get_last_system(gpu.handle, ep, ec, b)
+        torch.cuda.synchronize()
+        bn = b.cpu().numpy()
+        ora.set_sketch(Y.cpu().numpy().reshape(k, m).T)
+        ora.assemble(ep.cpu().numpy(), ec.cpu().numpy())
+        x0, rank = ora.ewma_guess(bn)
+        gres = np.linalg.norm(bn - ora.matvec(x0)) / np.linalg.norm(bn)
+        x, so, code = ora.gmres(bn, x0)
+        assert code == 0
+        rows.append((sg["guess_res"], gres, sg["iterations"], so["iterations"]))
+    gpu.close()
+    r = np.array(rows)
+    rel = np.abs(r[:, 0] - r[:, 1]) / r[:, 1]
+    assert rel.max() < 1e-6, (rel.max(), r)
+    d = r[:, 2] - r[:, 3]
+    assert np.all(np.abs(d) <= 1), r[:, 2:].T
+    assert np.count_nonzero(d) <= len(d) // 5, r[:, 2:].T

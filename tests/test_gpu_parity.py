@@ -289,3 +289,51 @@ def test_host_buffer_entry_point(sw):
     code = sw.solve_poisson_host(gpu.handle, np.ascontiguousarray(e1), np.ascontiguousarray(e2), b, xh)
     assert code == 0
     assert np.linalg.norm(xh - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_orthonormal_basis_guess_matches_oracle(sw, executor):
+    # V = Q (the optional QR step of Algorithms 3 and 4) on a fixed sketch: the same
+    # x0 as the oracle's Gram-Schmidt basis (a well-conditioned sketch drops no column)
+    nx, nz, L = 64, 9, 2 * math.pi
+    x64 = np.arange(nx) * (L / nx)
+    h = 1.0 - 0.3 * np.exp(-3 * (x64 - 3.0) ** 2)
+    k = 6
+    kw = dict(k=k, guess="ewma", orthonormalize=True)
+    gpu = sw.Problem(nx, 1, nz, L, 0.0, h, executor=executor, **kw)
+    ora = O.OracleProblem(nx, 1, nz, L, 0.0, h, **kw)
+    rng = np.random.default_rng(19)
+    Y = rng.standard_normal((ora.m, k)) @ np.triu(rng.uniform(0.5, 2.0, (k, k)))
+    ora.set_sketch(Y)
+    sw.set_sketch(gpu.handle, _t(Y.T.ravel()), 0)
+    e1, e2 = _surfaces(nx, 1, 20)
+    b = _rhs(ora, nz, 21)
+    ora.assemble(e1, e2)
+    x0o, rank = ora.ewma_guess(b)
+    x0 = torch.empty(gpu.m, dtype=torch.float64, device=DEV)
+    sw.subspace_guess(gpu.handle, _t(e1), _t(e2), _t(b), x0)
+    torch.cuda.synchronize()
+    err = np.linalg.norm(x0.cpu().numpy() - x0o) / np.linalg.norm(x0o)
+    assert rank == k and err < 1e-10, err
+
+
+@pytest.mark.parametrize("guess", ["ewma", "rrf"])
+@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+def test_orthonormal_basis_trajectory(sw, guess, executor):
+    wl = W.airy_2d()
+    kw = dict(restart=20, max_restarts=100, tol=1e-8, guess=guess, k=8, decay=0.9, n_init_solves=10,
+              orthonormalize=True)
+    rec = _record(wl, 8, **kw)
+    gpu = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], executor=executor, **kw)
+    x = torch.zeros(gpu.m, dtype=torch.float64, device=DEV)
+    diffs = []
+    for ep, ec, b, p, so in rec:
+        gpu.solve(_t(ep), _t(ec), _t(b), x)
+        sg = gpu.stats()
+        assert sg["status"] == 0
+        diffs.append(sg["iterations"] - so["iterations"])
+        err = np.linalg.norm(x.cpu().numpy() - p) / np.linalg.norm(p)
+        assert err < 1e-6, err
+    diffs = np.array(diffs)
+    assert np.all(np.abs(diffs) <= 1), diffs
+    assert np.count_nonzero(diffs) <= len(diffs) // 5, diffs
