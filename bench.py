@@ -77,9 +77,30 @@ def workload():
     return W.stokes_like_2d(nx=512, nz=17, kh=2.0, a1_over_h=0.08, steps=1000)
 
 
+N_INIT_STEPS = 6   # the paper's warm-up of the subspace method: 6 steps on the previous solution (Sec. 5.1)
+
+
 def solver_kw(args, guess):
-    return dict(restart=20, max_restarts=500, tol=1e-8, guess=guess, k=args.k, decay=args.decay, n_init_solves=30,
-                seed=2511, executor=getattr(args, "executor", "auto"))
+    return dict(restart=20, max_restarts=500, tol=1e-8, guess=guess, k=args.k, decay=args.decay,
+                n_init_solves=5 * N_INIT_STEPS, seed=2511, executor=getattr(args, "executor", "auto"))
+
+
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 # ---------------------------------------------------------------------------
@@ -143,8 +164,8 @@ class ClockSampler:
 # CPU baseline: the oracle as it stands, serial, on a bounded sample
 # ---------------------------------------------------------------------------
 def oracle_run(args, warm_steps, timed_steps, budget_s=None):
-    import numpy as np
-
+    """The serial oracle on the benchmark's trajectory: warm_steps untimed
+    steps (history fill included), then up to timed_steps timed steps."""
     import oracle as O
     import workloads as W
     wl = workload()
@@ -168,18 +189,45 @@ def oracle_run(args, warm_steps, timed_steps, budget_s=None):
     return n / dt, its / max(n, 1), n, dt
 
 
+def _oracle_worker(a):
+    ns, warm, timed, budget = a
+    return oracle_run(argparse.Namespace(**ns), warm, timed, budget_s=budget)
+
+
+def oracle_all_cores(args, warm_steps, timed_steps, budget_s):
+    """The serial oracle as one independent replica per host core (spawned
+    processes, no GPU in them): aggregate solves/s of the host."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    ns = {"k": args.k, "decay": args.decay, "executor": "auto"}
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(n) as pool:
+        res = pool.map(_oracle_worker, [(ns, warm_steps, timed_steps, budget_s)] * n)
+    wall = time.perf_counter() - t0
+    rate = sum(r[0] for r in res)
+    return {"value": rate, "unit": UNIT, "cores": n, "processes": n, "cpu_model": cpu_model(),
+            "iters_per_solve": statistics.mean(r[1] for r in res), "solves": int(sum(r[2] for r in res)),
+            "wall_s": wall, "kind": "oracle",
+            "sample": "%d independent replicas of the serial oracle, one per core, each %d untimed steps then "
+                      "up to %d timed steps (stopped after %.0f s)" % (n, warm_steps, timed_steps, budget_s)}
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
-    rate, its, n, dt = oracle_run(args, args.warmup, args.steps, budget_s=150.0)
+    warm = N_INIT_STEPS + args.warmup
+    allc = oracle_all_cores(args, warm, args.steps, 120.0)
+    rate = allc["value"]
+    ser_rate, ser_its, n1, dt1 = oracle_run(args, warm, args.steps, budget_s=60.0)
     line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 5000.0 * dt / n if n else None, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 5000.0 / rate, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "iters_per_solve": its,
+            "iters_per_solve": allc["iters_per_solve"],
             "config": {"workload": WORKLOAD, "guess": "ewma", "k": args.k, "decay": args.decay, "tol": 1e-8,
-                       "restart": 20},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d solves after %d warm-up steps (stopped after 150 s)" % (n, args.warmup)},
+                       "restart": 20, "history_fill_steps_untimed": N_INIT_STEPS},
+            "cpu_baseline": dict(allc, serial={"value": ser_rate, "cores": 1, "iters_per_solve": ser_its,
+                                               "solves": n1}),
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -254,9 +302,12 @@ def gpu_arm(args, rank, world, local_rank):
         import torch.distributed as dist
     wl = workload()
     t = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    # untimed before every timed window: the history fill of the subspace
+    # method (N_INIT_STEPS steps on the previous solution), then the warm-up
+    pre = N_INIT_STEPS + args.warmup
 
-    def make(guess):
-        P = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **solver_kw(args, guess))
+    def make(guess, precision="fp64"):
+        P = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], precision=precision, **solver_kw(args, guess))
         sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
         sw.set_state(P.handle, t(wl["u"]), None, t(wl["w"]), t(wl["eta"]))
         return P
@@ -264,7 +315,7 @@ def gpu_arm(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MiB > L2
     # ---- accelerated (EWMA) ----
     P = make("ewma")
-    run_steps(sw, torch, P, args.warmup)
+    run_steps(sw, torch, P, pre)
     torch.cuda.synchronize()
     s0 = sw.get_stats(P.handle)
     ph0 = sw.get_phase_times(P.handle)
@@ -289,44 +340,40 @@ def gpu_arm(args, rank, world, local_rank):
     sw.enable_timing(P.handle, False)
     s1 = sw.get_stats(P.handle)
     ph1 = sw.get_phase_times(P.handle)
+    P.close()
     nsolves = 5 * args.steps
     value, total_ms = replica_value(total_ms, nsolves, world, dist, dev)
     its = (s1["total_iterations"] - s0["total_iterations"]) / nsolves
     mflops = s1["model_flops"] - s0["model_flops"]
     mbytes = s1["model_bytes"] - s0["model_bytes"]
     launches = s1["launches"] - s0["launches"]
-    # ---- plain FP64 cold start and the previous-solution baseline on the same trajectory ----
+    # ---- plain FP64 cold start, the previous-solution baseline and the
+    # precision form: same workload, same untimed steps, same timed window ----
     base = {}
-    for guess in ("cold", "previous"):
-        Q = make(guess)
-        run_steps(sw, torch, Q, 2)
+    for guess, prec in (("cold", "fp64"), ("previous", "fp64"), ("ewma", "mixed")):
+        Q = make(guess, prec)
+        run_steps(sw, torch, Q, pre)
         torch.cuda.synchronize()
-        q0 = sw.get_stats(Q.handle)
-        qp0 = sw.get_phase_times(Q.handle)
-        ev = []
-        run_steps(sw, torch, Q, args.plain_steps, flush=flush, events=ev)
-        torch.cuda.synchronize()
-        q1 = sw.get_stats(Q.handle)
-        qp1 = sw.get_phase_times(Q.handle)
-        ms = sum(a.elapsed_time(b) for a, b in ev)
-        n = 5 * args.plain_steps
-        nit = q1["total_iterations"] - q0["total_iterations"]
-        base[guess] = {"value": n / (ms / 1e3), "iters_per_solve": nit / n,
-                       "ms_per_solve": ms / n, "steps": args.plain_steps,
-                       "phase_us_per_iteration": {k: round((qp1[k] - qp0[k]) / max(nit, 1), 2) for k in qp1}}
+        r = _timed_steps(sw, torch, Q, args.steps, flush)
         Q.close()
-    # ---- the precision form on the same trajectory ----
-    Mx = _make(sw, torch, dev, wl, "ewma", "mixed", args)
-    run_steps(sw, torch, Mx, args.warmup)
-    torch.cuda.synchronize()
-    mixed_res = _timed_steps(sw, torch, Mx, args.steps, flush)
-    Mx.close()
+        nit = r["iters_per_solve"] * nsolves
+        base[guess + "_" + prec] = {
+            "value": r["value"], "iters_per_solve": r["iters_per_solve"], "ms_per_solve": r["ms_per_step"] / 5,
+            "steps": args.steps,
+            "phase_us_per_iteration": {k: round(v * nsolves / max(nit, 1), 2) for k, v in r["phase_us_per_solve"].items()}}
+    # ---- error of every timed solve against the FP64 oracle (both forms): the
+    # same runs repeated untimed (the library is deterministic: same counts),
+    # each solve's system and solution recorded and re-solved by the oracle ----
+    errs = {}
+    for prec in ("fp64", "mixed"):
+        errs[prec] = _solve_errors(sw, torch, dev, wl, make("ewma", prec), pre, args.steps)
     # ---- end to end through the host-buffer C-ABI call ----
     e2e = None
+    oracle_cold = None
     if not args.no_e2e:
         R = make("ewma")
         m, ncol = R.m, R.ncol
-        nrec = args.warmup + args.steps
+        nrec = pre + args.steps
         rec_ep = torch.empty((nrec * 5, ncol), dtype=torch.float64, pin_memory=True)
         rec_ec = torch.empty_like(rec_ep)
         rec_b = torch.empty((nrec * 5, m), dtype=torch.float64, pin_memory=True)
@@ -343,11 +390,11 @@ def gpu_arm(args, rank, world, local_rank):
         R.close()
         E = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **solver_kw(args, "ewma"))
         xh = torch.empty(m, dtype=torch.float64, pin_memory=True)
-        for q in range(args.warmup * 5):
+        for q in range(pre * 5):
             sw.solve_poisson_host(E.handle, rec_ep[q], rec_ec[q], rec_b[q], xh)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for q in range(args.warmup * 5, nrec * 5):
+        for q in range(pre * 5, nrec * 5):
             sw.solve_poisson_host(E.handle, rec_ep[q], rec_ec[q], rec_b[q], xh)
         e2e_s = time.perf_counter() - t0
         E.close()
@@ -358,6 +405,9 @@ def gpu_arm(args, rank, world, local_rank):
         e2e = {"value": world * nsolves / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 5 * (2 * ncol + m) * 8, "d2h_bytes_per_step": 5 * m * 8,
                "note": "sw_solve_poisson_host on the recorded systems of the same trajectory"}
+        if rank == 0:
+            oracle_cold = _oracle_cold_orders(wl, [(rec_ep[q].numpy(), rec_ec[q].numpy(), rec_b[q].numpy())
+                                                  for q in (pre * 5, pre * 5 + 2)])
     if rank != 0:
         return
     peaks = load_peaks()
@@ -373,28 +423,96 @@ def gpu_arm(args, rank, world, local_rank):
             "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": peaks.get("hbm_gbs"),
                     "frac": (achieved_gbs / peaks["hbm_gbs"]) if achieved_gbs and peaks.get("hbm_gbs") else None},
             "kernel_ms_per_launch": solve_ms / max(n_timed, 1), "launches_timed": n_timed,
-            "kernel_share_of_step": solve_ms / total_ms if total_ms else None}
+            "kernel_share_of_step": solve_ms / total_ms if total_ms else None,
+            "note": "latency-bound at this size (9,216 unknowns, L2-resident); see roofline_large"}
     cpu = None
     if not args.no_cpu_baseline:
-        rate, cits, n, dt = oracle_run(args, 6, 40, budget_s=20.0)
+        rate, cits, n, dt = oracle_run(args, pre, args.steps, budget_s=20.0)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "iters_per_solve": cits,
-               "sample": "%d EWMA solves of the same workload after 6 warm-up steps, serial FP64 C oracle (%.1f s)"
-                         % (n, dt)}
+               "cpu_model": cpu_model(),
+               "sample": "%d EWMA solves of the same workload and window (%d untimed steps first), serial FP64 C "
+                         "oracle (%.1f s)" % (n, pre, dt),
+               "all_cores": oracle_all_cores(args, pre, args.steps, 20.0)}
+    cold, prev, mixed = base["cold_fp64"], base["previous_fp64"], base["ewma_mixed"]
+    if oracle_cold:
+        cold["oracle_cold_start_iters"] = oracle_cold
+    mixed_out = {k: mixed[k] for k in ("value", "iters_per_solve", "ms_per_solve")}
+    mixed_out["error_vs_fp64_oracle"] = errs["mixed"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "iters_per_solve": its, "us_per_solve": 1e3 * total_ms / nsolves,
-            "plain": base["cold"], "previous": base["previous"],
-            "mixed": {k: mixed_res[k] for k in ("value", "iters_per_solve", "ms_per_step")},
-            "speedup_vs_plain": value / base["cold"]["value"] / world,
+            "plain": cold, "previous": prev, "mixed": mixed_out,
+            "error_vs_fp64_oracle": errs["fp64"],
+            "speedup_vs_plain": value / cold["value"] / world,
+            "speedup_vs_previous": value / prev["value"] / world,
             "config": {"workload": WORKLOAD, "nx": 512, "nz": 17, "unknowns": wl["m"], "guess": "ewma", "k": args.k,
-                       "decay": args.decay, "tol": 1e-8, "restart": 20, "n_init_steps": 6, "dt": wl["dt"],
+                       "decay": args.decay, "tol": 1e-8, "restart": 20, "n_init_steps": N_INIT_STEPS,
+                       "history_fill_steps_untimed": N_INIT_STEPS, "dt": wl["dt"],
+                       "window": "every guess mode: %d untimed steps (history fill + warm-up), then the same %d "
+                                 "timed steps" % (pre, args.steps),
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches, "launches_per_solve": launches / nsolves, "wall_s_timed": wall,
             "phase_us_per_solve": {k: round((ph1[k] - ph0[k]) / nsolves, 2) for k in ph1}}
     print(json.dumps(line), flush=True)
+
+
+def _solve_errors(sw, torch, dev, wl, P, pre, steps):
+    """Run P untimed through pre + steps steps; for every solve of the last
+    `steps` steps, its relative error against the oracle's solution of the same
+    system (warm-started from the library's solution, tol 1e-12)."""
+    import numpy as np
+
+    import oracle as O
+    run_steps(sw, torch, P, pre)
+    ep = torch.empty(P.ncol, dtype=torch.float64, device=dev)
+    ec = torch.empty_like(ep)
+    b = torch.empty(P.m, dtype=torch.float64, device=dev)
+    x = torch.empty(P.m, dtype=torch.float64, device=dev)
+    recs = []
+    for _ in range(5 * steps):
+        sw.advance_stage(P.handle)
+        sw.get_last_system(P.handle, ep, ec, b)
+        sw.get_state(P.handle, pres=x)
+        st = sw.get_stats(P.handle)
+        recs.append((ep.cpu().numpy(), ec.cpu().numpy(), b.cpu().numpy(), x.cpu().numpy(), st["iterations"],
+                     st["true_res"]))
+    P.close()
+    ora = O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], restart=20, max_restarts=500, tol=1e-12)
+    e = []
+    for epn, ecn, bn, xn, _, _ in recs:
+        ora.assemble(epn, ecn)
+        xo, so, code = ora.gmres(bn, xn)
+        e.append(np.linalg.norm(xn - xo) / np.linalg.norm(xo))
+    e = np.array(e)
+    tr = np.array([r[5] for r in recs])
+    return {"max": float(e.max()), "mean": float(e.mean()), "solves": len(e), "true_res_max": float(tr.max()),
+            "reference": "oracle GMRES to 1e-12 on each solve's system, started from the library's solution",
+            "iters_per_solve": float(np.mean([r[4] for r in recs]))}
+
+
+def _oracle_cold_orders(wl, systems):
+    """Cold-start GMRES(20) iterations of the oracle on sample systems with its
+    colour-column ILU order (the library's) and with the natural x-fastest order."""
+    import numpy as np
+
+    import oracle as O
+    out = {}
+    for name in ("colour", "natural"):
+        ora = O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], restart=20, max_restarts=500, tol=1e-8)
+        if name == "natural":
+            ora.build_ilu(np.arange(ora.m, dtype=np.int32))
+        its = []
+        for epn, ecn, bn in systems:
+            ora.assemble(epn, ecn)
+            _, so, _ = ora.gmres(bn)
+            its.append(so["iterations"])
+        out[name + "_order"] = float(np.mean(its))
+    out["systems"] = len(systems)
+    out["note"] = "oracle cold starts on systems of the timed window; the library uses the colour order"
+    return out
 
 
 def _t(torch, dev, a):

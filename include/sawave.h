@@ -56,6 +56,8 @@ extern "C" {
 #define SW_ERR_NOT_CONVERGED (-3)    /* iteration cap reached; x holds the last iterate */
 #define SW_ERR_SINGULAR_PRECOND (-4) /* zero pivot in the ILU factorisation */
 #define SW_ERR_NAN (-5)              /* non-finite residual during a solve */
+#define SW_ERR_TIMEOUT (-6)          /* a wait inside a solve kernel ran past its bound (2 s of device time);
+                                        the solve was abandoned and x is incomplete */
 
 #define SW_GUESS_COLD 0      /* x0 = 0 */
 #define SW_GUESS_PREVIOUS 1  /* x0 = previous solution (the paper's baseline, Sec. 5.1) */
@@ -74,6 +76,12 @@ extern "C" {
                                  between, one stream synchronisation per restart cycle: keeps HBM
                                  busy on large problems (sw_solve_poisson then returns once the
                                  solve has finished) */
+#define SW_EXEC_RESIDENT 3    /* small periodic 2-D FP64 problems: one block per slab of columns with the
+                                 slab's vectors and constants in shared memory; neighbouring blocks
+                                 exchange boundary columns through flags (no grid barrier) and inner
+                                 products are all-reduced with one atomic per block; same arithmetic
+                                 up to rounding, the norm of the twice-orthogonalised Krylov vector from
+                                 ||w||^2 - ||h'||^2 */
 #define SW_EXEC_STREAMED_MIN 262144
 
 typedef struct sw_problem sw_problem;
@@ -271,9 +279,11 @@ int sw_batch_advance_stage(sw_batch *b, void *stream);
  * Scratch lives in one static device array sized for at most 65,536 columns
  * (nx*ny; about 12.6 MB held by every GPU that loads the library until exit);
  * larger grids return SW_ERR_BAD_ARG.  The first call on a device resolves
- * the array's address and should come before any stream capture.  Calls share
- * the array: two calls that overlap on the GPU race.  Same grid rules as
- * sw_create_problem; periodic grids only (walls: SW_ERR_BAD_ARG). */
+ * the array's address and should come before any stream capture.  A call
+ * enqueues kernels only (the weights travel as kernel arguments, no copy from
+ * host memory).  Calls share the array: two calls that overlap on the GPU
+ * race.  Same grid rules as sw_create_problem; periodic grids only (walls:
+ * SW_ERR_BAD_ARG). */
 int sw_apply_operator_noalloc(const sw_grid *grid, const double *d_h, const double *d_eta_prev,
                               const double *d_eta_cur, const double *d_x, double *d_y, void *stream);
 
@@ -291,6 +301,14 @@ int sw_get_solve_time(sw_problem *p, double *total_ms, long long *n_timed);
  * 6 Arnoldi apply, 7 Arnoldi preconditioner, 8-10 the three Gram-Schmidt
  * passes, 11 Givens rotations, 12 solution update, 13 true residual. */
 int sw_get_phase_times(sw_problem *p, double *us, int n);
+
+/* Testing aid for failure detection without a GPU fault: in the next solve of
+ * a problem on the resident executor, block 0 stops raising its flag from its
+ * `exchange`-th boundary exchange on (1 = the first), so the neighbouring
+ * blocks' bounded waits run out, every block leaves the kernel and the solve's
+ * status (sw_get_stats) is SW_ERR_TIMEOUT; later solves are unaffected.
+ * SW_ERR_BAD_ARG for another executor or exchange < 1. */
+int sw_test_stall_exchange(sw_problem *p, int exchange);
 
 /* Last error message of the calling thread (static storage). */
 const char *sw_last_error(void);

@@ -15,14 +15,14 @@ __all__ = ["Grid", "Params", "Stats", "Physics", "Problem", "create_problem", "d
            "solve_poisson", "solve_poisson_host", "get_stats", "apply_operator", "apply_preconditioner",
            "subspace_guess", "apply_operator_noalloc", "get_sketch", "set_sketch", "draw_omega", "set_physics", "set_state", "get_state",
            "advance_stage", "set_relaxation", "set_step", "Relaxation", "create_batch", "destroy_batch", "batch_solve", "batch_advance_stage", "Batch",
-           "get_last_system", "get_phase_times", "enable_timing", "get_solve_time", "library_path", "SawaveError", "GUESS",
+           "get_last_system", "get_phase_times", "enable_timing", "get_solve_time", "test_stall_exchange", "library_path", "SawaveError", "GUESS",
            "PRECISION", "EXECUTOR"]
 
 SW_OK = 0
-STATUS = {0: "OK", -1: "BAD_ARG", -2: "CUDA_ERR", -3: "NOT_CONVERGED", -4: "SINGULAR_PRECOND", -5: "NAN"}
+STATUS = {0: "OK", -1: "BAD_ARG", -2: "CUDA_ERR", -3: "NOT_CONVERGED", -4: "SINGULAR_PRECOND", -5: "NAN", -6: "TIMEOUT"}
 GUESS = {"cold": 0, "previous": 1, "ewma": 2, "rrf": 3}
 PRECISION = {"fp64": 0, "mixed": 1}
-EXECUTOR = {"auto": 0, "persistent": 1, "streamed": 2}
+EXECUTOR = {"auto": 0, "persistent": 1, "streamed": 2, "resident": 3}
 
 
 class SawaveError(RuntimeError):
@@ -107,6 +107,7 @@ def lib():
         L.sw_batch_advance_stage.argtypes = [vp, vp]
         L.sw_batch_set_cluster.argtypes = [vp, ip]
         L.sw_get_solve_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.sw_test_stall_exchange.argtypes = [vp, ip]
         L.sw_last_error.restype = C.c_char_p
         for name in ["sw_create_problem", "sw_destroy_problem", "sw_problem_size", "sw_solve_poisson",
                      "sw_solve_poisson_host", "sw_get_stats", "sw_apply_operator", "sw_apply_preconditioner",
@@ -254,6 +255,11 @@ def set_relaxation(p, relax):
 
 def set_step(p, n_steps):
     return _check(lib().sw_set_step(p, int(n_steps)))
+
+
+def test_stall_exchange(p, exchange):
+    """Testing aid: the next resident solve withholds block 0's flag at this exchange (see sawave.h)."""
+    return _check(lib().sw_test_stall_exchange(p, int(exchange)))
 
 
 def get_last_system(p, eta_prev=None, eta_cur=None, b=None, stream=None):

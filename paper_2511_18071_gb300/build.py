@@ -23,7 +23,7 @@ UNITS = ([("batch_kernel.cu", "batch_%s.o" % t, ["-DSW_TI=%s" % ti, "-DSW_CLUSTE
                                                   "-DSW_NAME=batch_kernel_%s" % t]) for t, ti, c in _BATCH] +
          [("solve_kernel.cu", "solve_%s.o" % t, ["-DSW_TI=%s" % ti, "-DSW_WM=(%s)" % wm,
                                                   "-DSW_NAME=solve_kernel_%s" % t]) for t, ti, wm in _SOLVE] +
-         [(f, f.replace(".cu", ".o"), []) for f in ("streamed.cu", "setup.cu", "solver.cu", "driver.cu", "batch.cu",
+         [(f, f.replace(".cu", ".o"), []) for f in ("resident.cu", "streamed.cu", "setup.cu", "solver.cu", "driver.cu", "batch.cu",
                                                      "noalloc.cu")])
 SOURCES = sorted({u[0] for u in UNITS})
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -13,12 +13,15 @@
 // 12.6 MB); every GPU that loads the library keeps it until the process exits.
 // On the first call on a device (with that device current) the host resolves
 // the array's device address with cudaGetSymbolAddress and sets the kernel
-// attributes; that first call should come before any stream capture.  All
-// calls share the one array and every call rewrites everything it reads, so
-// nothing needs clearing between calls, but two calls that overlap on the GPU
-// (different streams, or different host threads) race on it.
+// attributes; that first call should come before any stream capture.  The
+// weights travel to the device as a kernel argument, so a call issues kernel
+// launches only.  All calls share the one array and every call rewrites
+// everything it reads, so nothing needs clearing between calls, but two calls
+// that overlap on the GPU (different streams, or different host threads) race
+// on it.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "sw_device.cuh"
 
@@ -40,9 +43,24 @@ static_assert(NCC <= NA_CC, "coefficient region");
 
 static __device__ __align__(256) double g_noalloc_scratch[NA_TOTAL];
 
-// Host-side copy of the array's device address, per device.
+// Host-side copy of the array's device address, per device, set once under
+// the mutex.
 constexpr int NA_MAX_DEVICES = 64;
 double *g_dev_ptr[NA_MAX_DEVICES] = {};
+std::mutex g_setup_mutex;
+
+// Weights and sigma windows of one call, passed by value (7.6 KB of kernel
+// arguments) to the kernel that installs them in the array.
+struct NaHead {
+    double w[NA_WEIGHTS];
+    int win[MAX_LEVELS];
+};
+
+__global__ void na_install_kernel(NaHead hd, double *base) {
+    for (int i = threadIdx.x; i < NA_WEIGHTS; i += blockDim.x) base[i] = hd.w[i];
+    int *win = reinterpret_cast<int *>(base + NA_HEAD);
+    for (int i = threadIdx.x; i < MAX_LEVELS; i += blockDim.x) win[i] = hd.win[i];
+}
 
 struct NaLoad {
     const double *v;
@@ -88,25 +106,6 @@ __global__ void __launch_bounds__(NTHREADS) na_apply_kernel(Dev D, Tiling tl, co
     for (int tile = blockIdx.x; tile < tl.ntiles; tile += gridDim.x) apply_tile<double>(D, tl, tile, sp, sq, ld, st);
 }
 
-// 7-point weights from the derivatives of the Lagrange basis polynomials.
-void na_weights(const long double *x, long double z, double *w1, double *w2) {
-    for (int i = 0; i < W; ++i) {
-        long double c[W] = {1.0L};
-        int deg = 0;
-        long double den = 1.0L;
-        for (int q = 0; q < W; ++q) {
-            if (q == i) continue;
-            long double r = x[q] - z;
-            for (int p = deg + 1; p >= 1; --p) c[p] = c[p - 1] - r * c[p];
-            c[0] = -r * c[0];
-            ++deg;
-            den *= (x[i] - x[q]);
-        }
-        w1[i] = (double)(c[1] / den);
-        w2[i] = (double)(2.0L * c[2] / den);
-    }
-}
-
 Tiling na_tiling(const Dev &D) {
     Tiling t{};
     if (!D.three_d) {
@@ -140,6 +139,7 @@ int na_setup(double **out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= NA_MAX_DEVICES) { set_error("device index out of range"); return SW_ERR_BAD_ARG; }
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_dev_ptr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -181,30 +181,15 @@ extern "C" int sw_apply_operator_noalloc(const sw_grid *grid, const double *d_h,
     cudaStream_t s = (cudaStream_t)stream;
     const int P = g.nz + 1;
     const int ncol = g.nx * g.ny;
-    // weights and sigma windows, staged on the host stack and copied in
-    double head[NA_HEAD + NA_WIN];
-    std::memset(head, 0, sizeof(head));
+    // weights and sigma windows (the same host builder as sw_create_problem),
+    // installed by a kernel that receives them by value
+    NaHead hd;
+    std::memset(&hd, 0, sizeof(hd));
     {
-        long double xs[W];
-        double dx = g.lx / g.nx, dy = three_d ? g.ly / g.ny : 1.0;
-        for (int t = 0; t < W; ++t) xs[t] = (long double)(t - HALF) * (long double)dx;
-        na_weights(xs, 0.0L, head, head + W);
-        for (int t = 0; t < W; ++t) xs[t] = (long double)(t - HALF) * (long double)dy;
-        na_weights(xs, 0.0L, head + 2 * W, head + 3 * W);
-        int win[MAX_LEVELS] = {0};
-        for (int j = -1; j < g.nz; ++j) {
-            int s0 = j - HALF;
-            if (s0 < -1) s0 = -1;
-            if (s0 > g.nz - W) s0 = g.nz - W;
-            win[j + 1] = s0;
-            for (int k = 0; k < W; ++k) xs[k] = (long double)(s0 + k) / (long double)(g.nz - 1);
-            na_weights(xs, (long double)j / (long double)(g.nz - 1), head + 4 * W + (j + 1) * W,
-                       head + 4 * W + P * W + (j + 1) * W);
-        }
-        std::memcpy(head + NA_HEAD, win, sizeof(win));
+        const sw_grid gp = {g.nx, g.ny, g.nz, g.lx, three_d ? g.ly : 0.0, 0};
+        grid_weights(gp, hd.w, hd.w + W, hd.w + 2 * W, hd.w + 3 * W, hd.w + 4 * W, hd.w + 4 * W + P * W, hd.win);
     }
-    cudaError_t e = cudaMemcpyAsync(base, head, sizeof(head), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "weights copy");
+    na_install_kernel<<<1, 256, 0, s>>>(hd, base);
     double *hder = base + NA_HEAD + NA_WIN;
     double *cc = hder + (size_t)NA_HDERIV * NA_COLS;
     Dev D{};
@@ -224,7 +209,7 @@ extern "C" int sw_apply_operator_noalloc(const sw_grid *grid, const double *d_h,
     Tiling tl = na_tiling(D);
     size_t smem = 2 * (size_t)P * tl.HW * sizeof(double);
     na_apply_kernel<<<tl.ntiles, NTHREADS, smem, s>>>(D, tl, d_x, d_y);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "noalloc apply launch");
     return SW_OK;
 }

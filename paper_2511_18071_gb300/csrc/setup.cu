@@ -32,7 +32,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 // Derivative weights at z from the Lagrange basis polynomials through nodes
 // x[0..6]: the d-th derivative of l_i at z is d! times the coefficient of
 // (x - z)^d in prod_{q != i} (x - x_q) / prod_{q != i} (x_i - x_q).
-static void lagrange_weights(const long double *x, long double z, double *w1, double *w2) {
+void lagrange_weights(const long double *x, long double z, double *w1, double *w2) {
     for (int i = 0; i < W; ++i) {
         long double c[W] = {1.0L};  // coefficients in powers of t = x - z
         int deg = 0;
@@ -50,11 +50,28 @@ static void lagrange_weights(const long double *x, long double z, double *w1, do
     }
 }
 
-static int sigma_window(int nz, int j) {
+int sigma_window(int nz, int j) {
     int s = j - HALF;
     if (s < -1) s = -1;
     if (s > nz - W) s = nz - W;
     return s;
+}
+
+void grid_weights(const sw_grid &g, double *wx1, double *wx2, double *wy1, double *wy2, double *ws1, double *ws2,
+                  int *win) {
+    const double dx = g.walls ? g.lx / (g.nx - 3) : g.lx / g.nx;
+    const double dy = g.ny > 1 ? g.ly / g.ny : 1.0;
+    long double xs[W];
+    for (int t = 0; t < W; ++t) xs[t] = (long double)(t - HALF) * (long double)dx;
+    lagrange_weights(xs, 0.0L, wx1, wx2);
+    for (int t = 0; t < W; ++t) xs[t] = (long double)(t - HALF) * (long double)dy;
+    lagrange_weights(xs, 0.0L, wy1, wy2);
+    for (int j = -1; j < g.nz; ++j) {
+        const int s0 = sigma_window(g.nz, j);
+        win[j + 1] = s0;
+        for (int k = 0; k < W; ++k) xs[k] = (long double)(s0 + k) / (long double)(g.nz - 1);
+        lagrange_weights(xs, (long double)j / (long double)(g.nz - 1), ws1 + (j + 1) * W, ws2 + (j + 1) * W);
+    }
 }
 
 namespace {
@@ -422,7 +439,7 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     if (p.restart < 1 || p.restart > MAX_RESTART || p.max_restarts < 0 || !(p.tol > 0) || p.guess < 0 ||
         p.guess > 3 || p.k < 1 || p.k > MAX_K || !(p.decay > 0) || p.decay > 1 || p.n_init_solves < 0 ||
         (p.precision != SW_PRECISION_FP64 && p.precision != SW_PRECISION_MIXED) || p.executor < 0 ||
-        p.executor > 2) {
+        p.executor > SW_EXEC_RESIDENT) {
         set_error("params: restart 1..32, k 1..16, decay in (0,1], tol > 0, known guess/precision/executor");
         return SW_ERR_BAD_ARG;
     }
@@ -442,21 +459,12 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
     H.layout = three_d ? (flat ? CROSS3D : BOX3D) : (flat ? CROSS2D : BOX2D);
     H.nslot = layout_nslot(H.layout);
     {
-        long double xs[W];
-        for (int t = 0; t < W; ++t) xs[t] = (long double)(t - HALF) * (long double)H.dx;
-        lagrange_weights(xs, 0.0L, H.wx1, H.wx2);
+        H.ws1.resize(H.P * W); H.ws2.resize(H.P * W); H.win.resize(H.P);
+        grid_weights(g, H.wx1, H.wx2, H.wy1, H.wy2, H.ws1.data(), H.ws2.data(), H.win.data());
         // walls: every evaluation point o of a window of 7 equispaced nodes
+        long double xs[W];
         for (int t = 0; t < W; ++t) xs[t] = (long double)t * (long double)H.dx;
         for (int o = 0; o < W; ++o) lagrange_weights(xs, (long double)o * (long double)H.dx, H.wxo1[o], H.wxo2[o]);
-        for (int t = 0; t < W; ++t) xs[t] = (long double)(t - HALF) * (long double)H.dy;
-        lagrange_weights(xs, 0.0L, H.wy1, H.wy2);
-        H.ws1.resize(H.P * W); H.ws2.resize(H.P * W); H.win.resize(H.P);
-        for (int j = -1; j < g.nz; ++j) {
-            int s0 = sigma_window(g.nz, j);
-            H.win[j + 1] = s0;
-            for (int k = 0; k < W; ++k) xs[k] = (long double)(s0 + k) / (long double)(g.nz - 1);
-            lagrange_weights(xs, (long double)j / (long double)(g.nz - 1), &H.ws1[(j + 1) * W], &H.ws2[(j + 1) * W]);
-        }
     }
     // surface-grid derivatives of the bathymetry (D_chi, D_gamma of Sec. 3);
     // with walls over the physical columns, a ghost column taking its wall column's
@@ -684,12 +692,14 @@ extern "C" int sw_create_problem(const sw_grid *grid, const sw_params *params, c
 
 namespace sw {
 void destroy_streamed(Problem *P);   // streamed.cu
+void destroy_resident(Problem *P);   // resident.cu
 }
 
 extern "C" int sw_destroy_problem(sw_problem *pp) {
     Problem *P = (Problem *)pp;
     if (!P) return SW_OK;
     destroy_streamed(P);
+    destroy_resident(P);
     for (auto ev : P->ev) cudaEventDestroy(ev);
     for (void *a : P->allocs) cudaFree(a);
     delete P;

@@ -123,6 +123,8 @@ static bool mixed(const Problem *P) { return P->params.precision == SW_PRECISION
 
 int setup_streamed(Problem *P);                                   // streamed.cu
 int solve_streamed(Problem *P, const SolveArgs &A, cudaStream_t s);  // streamed.cu
+int setup_resident(Problem *P);                                   // resident.cu
+int solve_resident(Problem *P, const SolveArgs &A, cudaStream_t s);  // resident.cu
 
 int setup_solver_launch(Problem *P) {
     int ex = P->params.executor;
@@ -130,6 +132,10 @@ int setup_solver_launch(Problem *P) {
     P->exec = ex;
     if (ex == SW_EXEC_STREAMED) {
         int rc = setup_streamed(P);
+        if (rc != SW_OK) return rc;
+    }
+    if (ex == SW_EXEC_RESIDENT) {
+        int rc = setup_resident(P);
         if (rc != SW_OK) return rc;
     }
     Tiling t = make_tiling(P->dev);
@@ -242,6 +248,9 @@ static int launch_solve(Problem *P, const double *ep, const double *ec, const do
     }
     if (P->exec == SW_EXEC_STREAMED) {
         int rc = solve_streamed(P, A, s);
+        if (rc != SW_OK) return rc;
+    } else if (P->exec == SW_EXEC_RESIDENT) {
+        int rc = solve_resident(P, A, s);
         if (rc != SW_OK) return rc;
     } else {
         const void *kern = solve_kernel_for(P);

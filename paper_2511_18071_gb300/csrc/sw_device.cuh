@@ -51,75 +51,81 @@ __device__ __forceinline__ int xwin_phys(const Dev &D, int ixp) { return min(max
 // derivatives with the fixed 7-point operators (Sec. 3), and the per-column
 // factors of sigma_x, sigma_y and 1/d used by every row (Eq. 13b-13d).
 // ---------------------------------------------------------------------------
+// Coefficients of column c (ghost columns of a walled grid take their wall
+// column's); out[k] is coefficient k of the CC_* list.
+__device__ inline void column_coefs(const Dev &D, const double *eta_prev, const double *eta_cur, int c,
+                                    double (&out)[NCC]) {
+    // x window: centred and periodic, or (walls, 2-D) over the physical
+    // columns; a ghost column takes the coefficients of its wall column
+    int ix = c % D.nx;
+    const int iy = c / D.nx;
+    int xs0 = ix - HALF;
+    const double *w1 = D.wx1, *w2 = D.wx2;
+    if (D.walls) {
+        ix = phys_col(D, ix);
+        xs0 = xwin_phys(D, ix);
+        w1 = D.wxo1 + (ix - xs0) * W;
+        w2 = D.wxo2 + (ix - xs0) * W;
+    }
+    const int ce = iy * D.nx + ix;   // column the coefficients are evaluated at
+    double dp1 = 0, dp2 = 0, dc1 = 0, dpy1 = 0, dpy2 = 0, dcy1 = 0;
+#pragma unroll
+    for (int t = -HALF; t <= HALF; ++t) {
+        int gx = xs0 + t + HALF;
+        if (!D.walls) gx = wrapi(gx, D.nx);
+        int cx = iy * D.nx + gx;
+        double vp = D.h[cx] + eta_prev[cx];
+        double vc = D.h[cx] + eta_cur[cx];
+        dp1 += w1[t + HALF] * vp;
+        dp2 += w2[t + HALF] * vp;
+        dc1 += w1[t + HALF] * vc;
+        if (D.three_d) {
+            int cy = wrapi(iy + t, D.ny) * D.nx + ix;
+            double wp = D.h[cy] + eta_prev[cy];
+            double wc = D.h[cy] + eta_cur[cy];
+            dpy1 += D.wy1[t + HALF] * wp;
+            dpy2 += D.wy2[t + HALF] * wp;
+            dcy1 += D.wy1[t + HALF] * wc;
+        }
+    }
+    double dp = D.h[ce] + eta_prev[ce], dcu = D.h[ce] + eta_cur[ce];
+    double f = 1.0 / dp, e = 1.0 / dcu;
+    double hx = D.hx[ce], hy = D.three_d ? D.hy[ce] : 0.0;
+    const double hxx = D.hxx[ce], hyy = D.three_d ? D.hyy[ce] : 0.0;
+    out[CC_F] = f;
+    out[CC_E] = e;
+    out[CC_EF] = e * f;
+    out[CC_AP0] = hx * f;
+    out[CC_AP1] = dp1 * f;
+    out[CC_AXP0] = hxx * f;
+    out[CC_AXP1] = dp2 * f;
+    out[CC_BP0] = hx * e;
+    out[CC_BP1] = dc1 * e;
+    // ghost row n . grad^(i-1) p at sigma = 0 with n = -(h_x, h_y, 1)/|(h_x, h_y, 1)|
+    double nrm = 1.0 / sqrt(1.0 + hx * hx + hy * hy);
+    out[CC_GS] = -nrm * (hx * hx * f + hy * hy * f + f);
+    out[CC_GX] = -nrm * hx;
+    out[CC_GY] = -nrm * hy;
+    out[CC_GN] = -nrm;
+    out[CC_AY0] = hy * f;
+    out[CC_AY1] = dpy1 * f;
+    out[CC_AYY0] = hyy * f;
+    out[CC_AYY1] = dpy2 * f;
+    out[CC_BY0] = hy * e;
+    out[CC_BY1] = dcy1 * e;
+}
+
 __device__ inline void geometry_columns(const Dev &D, const double *eta_prev, const double *eta_cur, int tid,
                                         int nth) {
     double *cc = D.gp;
     const int n = D.ncol;
     for (int c = tid; c < n; c += nth) {
-        // x window: centred and periodic, or (walls, 2-D) over the physical
-        // columns; a ghost column takes the coefficients of its wall column
-        int ix = c % D.nx;
-        const int iy = c / D.nx;
-        int xs0 = ix - HALF;
-        const double *w1 = D.wx1, *w2 = D.wx2;
-        if (D.walls) {
-            ix = phys_col(D, ix);
-            xs0 = xwin_phys(D, ix);
-            w1 = D.wxo1 + (ix - xs0) * W;
-            w2 = D.wxo2 + (ix - xs0) * W;
-        }
-        const int ce = iy * D.nx + ix;   // column the coefficients are evaluated at
-        double dp1 = 0, dp2 = 0, dc1 = 0, dpy1 = 0, dpy2 = 0, dcy1 = 0;
-#pragma unroll
-        for (int t = -HALF; t <= HALF; ++t) {
-            int gx = xs0 + t + HALF;
-            if (!D.walls) gx = wrapi(gx, D.nx);
-            int cx = iy * D.nx + gx;
-            double vp = D.h[cx] + eta_prev[cx];
-            double vc = D.h[cx] + eta_cur[cx];
-            dp1 += w1[t + HALF] * vp;
-            dp2 += w2[t + HALF] * vp;
-            dc1 += w1[t + HALF] * vc;
-            if (D.three_d) {
-                int cy = wrapi(iy + t, D.ny) * D.nx + ix;
-                double wp = D.h[cy] + eta_prev[cy];
-                double wc = D.h[cy] + eta_cur[cy];
-                dpy1 += D.wy1[t + HALF] * wp;
-                dpy2 += D.wy2[t + HALF] * wp;
-                dcy1 += D.wy1[t + HALF] * wc;
-            }
-        }
-        double dp = D.h[ce] + eta_prev[ce], dcu = D.h[ce] + eta_cur[ce];
-        double f = 1.0 / dp, e = 1.0 / dcu;
-        double hx = D.hx[ce], hy = D.three_d ? D.hy[ce] : 0.0;
-        const double hxx = D.hxx[ce], hyy = D.three_d ? D.hyy[ce] : 0.0;
-        cc[CC_F * n + c] = f;
-        cc[CC_E * n + c] = e;
-        cc[CC_EF * n + c] = e * f;
-        cc[CC_AP0 * n + c] = hx * f;
-        cc[CC_AP1 * n + c] = dp1 * f;
-        cc[CC_AXP0 * n + c] = hxx * f;
-        cc[CC_AXP1 * n + c] = dp2 * f;
-        cc[CC_BP0 * n + c] = hx * e;
-        cc[CC_BP1 * n + c] = dc1 * e;
-        // ghost row n . grad^(i-1) p at sigma = 0 with n = -(h_x, h_y, 1)/|(h_x, h_y, 1)|
-        double nrm = 1.0 / sqrt(1.0 + hx * hx + hy * hy);
-        cc[CC_GS * n + c] = -nrm * (hx * hx * f + hy * hy * f + f);
-        cc[CC_GX * n + c] = -nrm * hx;
-        cc[CC_GY * n + c] = -nrm * hy;
-        cc[CC_GN * n + c] = -nrm;
-        if (D.three_d) {
-            cc[CC_AY0 * n + c] = hy * f;
-            cc[CC_AY1 * n + c] = dpy1 * f;
-            cc[CC_AYY0 * n + c] = hyy * f;
-            cc[CC_AYY1 * n + c] = dpy2 * f;
-            cc[CC_BY0 * n + c] = hy * e;
-            cc[CC_BY1 * n + c] = dcy1 * e;
-        }
-        if (D.gp32) {
-            const int nc = D.three_d ? NCC : CC_GN + 1;
-            for (int k = 0; k < nc; ++k) D.gp32[k * n + c] = (float)cc[k * n + c];
-        }
+        double v[NCC];
+        column_coefs(D, eta_prev, eta_cur, c, v);
+        const int nc = D.three_d ? NCC : CC_GN + 1;
+        for (int k = 0; k < nc; ++k) cc[k * n + c] = v[k];
+        if (D.gp32)
+            for (int k = 0; k < nc; ++k) D.gp32[k * n + c] = (float)v[k];
     }
 }
 

@@ -136,6 +136,8 @@ struct Problem {
     int nblocks = 0, nthreads = 0;
     int exec = SW_EXEC_PERSISTENT;  // resolved executor of the solves
     void *streamed = nullptr;      // state of the streamed executor
+    void *resident = nullptr;      // state of the resident executor
+    int resident_stall = -1;       // testing aid of sw_test_stall_exchange (next solve only)
     size_t smem = 0;
     cudaStream_t last_stream = nullptr;
     bool has_state = false;
@@ -159,6 +161,18 @@ struct DevStats {
     double phase_ns[16];   // cumulative device time per solve phase (block 0's view)
 };
 
+
+// Host helpers of the finite-difference set-up (setup.cu), shared by every
+// entry point that builds weights.
+// 7-point derivative weights w1 (first) and w2 (second derivative) at z over
+// the nodes x[0..6], from the derivatives of the Lagrange basis polynomials.
+void lagrange_weights(const long double *x, long double z, double *w1, double *w2);
+// First level of the 7-level sigma window used at level j (j = -1..nz-1).
+int sigma_window(int nz, int j);
+// Centred x and y weights (7 each) and the sigma weights and windows of every
+// level (ws1, ws2: (nz + 1) x 7, row j + 1; win: nz + 1) of a grid.
+void grid_weights(const sw_grid &g, double *wx1, double *wx2, double *wy1, double *wy2, double *ws1, double *ws2,
+                  int *win);
 
 void set_error(const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);

@@ -99,9 +99,11 @@ def _rhs(ora, nz, seed):
 
 
 @pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
-@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+@pytest.mark.parametrize("executor", ["persistent", "streamed", "resident"])
 def test_cold_solve_tight(sw, case, executor):
     name, nx, ny, nz, lx, ly, h = case
+    if executor == "resident" and ny > 1:
+        pytest.skip("the resident executor serves 2-D problems")
     kw = dict(restart=20, max_restarts=300, tol=1e-12, guess="cold")
     gpu = sw.Problem(nx, ny, nz, lx, ly, h, executor=executor, **kw)
     ora = O.OracleProblem(nx, ny, nz, lx, ly, h, **kw)
@@ -140,7 +142,7 @@ def _record(wl, nsteps, **kw):
 
 
 @pytest.mark.parametrize("guess", ["previous", "ewma", "rrf"])
-@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+@pytest.mark.parametrize("executor", ["persistent", "streamed", "resident"])
 def test_trajectory_iterations_and_solutions(sw, guess, executor):
     wl = W.airy_2d()
     kw = dict(restart=20, max_restarts=100, tol=1e-8, guess=guess, k=8, decay=0.9, n_init_solves=10)
@@ -160,7 +162,7 @@ def test_trajectory_iterations_and_solutions(sw, guess, executor):
     assert np.count_nonzero(diffs) <= len(diffs) // 5, diffs
 
 
-@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+@pytest.mark.parametrize("executor", ["persistent", "streamed", "resident"])
 def test_sketch_after_solves_matches_oracle(sw, executor):
     wl = W.airy_2d()
     kw = dict(restart=20, max_restarts=100, tol=1e-12, guess="ewma", k=5, decay=0.8, n_init_solves=2)
@@ -179,7 +181,7 @@ def test_sketch_after_solves_matches_oracle(sw, executor):
     assert np.abs(Yg - Yo).max() <= 1e-9 * np.abs(Yo).max()
 
 
-@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+@pytest.mark.parametrize("executor", ["persistent", "streamed", "resident"])
 def test_subspace_guess_matches_oracle(sw, executor):
     nx, nz, L = 64, 9, 2 * math.pi
     x64 = np.arange(nx) * (L / nx)
@@ -203,7 +205,7 @@ def test_subspace_guess_matches_oracle(sw, executor):
     assert rank == k and err < 1e-10, err
 
 
-@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+@pytest.mark.parametrize("executor", ["persistent", "streamed", "resident"])
 def test_in_span_solution_needs_no_iterations(sw, executor):
     nx, nz, L = 64, 9, 2 * math.pi
     h = np.ones(nx)
@@ -224,7 +226,7 @@ def test_in_span_solution_needs_no_iterations(sw, executor):
     assert sg["status"] == 0 and sg["iterations"] == 0, sg
 
 
-@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+@pytest.mark.parametrize("executor", ["persistent", "streamed", "resident"])
 def test_zero_rhs_and_iteration_cap(sw, executor):
     nx, nz, L = 32, 9, 2 * math.pi
     gpu = sw.Problem(nx, 1, nz, L, 0.0, np.ones(nx), restart=2, max_restarts=0, tol=1e-14, executor=executor)
@@ -240,7 +242,7 @@ def test_zero_rhs_and_iteration_cap(sw, executor):
     assert sg["status"] == -3 and sg["iterations"] == 2 and not sg["converged"], sg
 
 
-@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+@pytest.mark.parametrize("executor", ["persistent", "streamed", "resident"])
 def test_nan_rhs_reported(sw, executor):
     nx, nz, L = 32, 9, 2 * math.pi
     gpu = sw.Problem(nx, 1, nz, L, 0.0, np.ones(nx), executor=executor)
@@ -252,7 +254,7 @@ def test_nan_rhs_reported(sw, executor):
     assert gpu.stats()["status"] == -5
 
 
-@pytest.mark.parametrize("executor", ["persistent", "streamed"])
+@pytest.mark.parametrize("executor", ["persistent", "streamed", "resident"])
 def test_stage_driver_matches_oracle(sw, executor):
     wl = W.airy_2d()
     kw = dict(restart=20, max_restarts=200, tol=1e-12, guess="previous")
@@ -337,3 +339,27 @@ def test_orthonormal_basis_trajectory(sw, guess, executor):
     diffs = np.array(diffs)
     assert np.all(np.abs(diffs) <= 1), diffs
     assert np.count_nonzero(diffs) <= len(diffs) // 5, diffs
+
+
+def test_resident_wait_bound_reports_timeout(sw):
+    # failure detection without a GPU fault: block 0 stops raising its flag at
+    # the third boundary exchange, its neighbours' bounded waits run out (2 s), every
+    # block leaves the kernel, the solve reports SW_ERR_TIMEOUT, and the next
+    # solve on the same problem and context succeeds
+    nx, nz, L = 64, 9, 2 * math.pi
+    kw = dict(restart=20, max_restarts=100, tol=1e-10, guess="cold")
+    gpu = sw.Problem(nx, 1, nz, L, 0.0, np.ones(nx), executor="resident", **kw)
+    ora = O.OracleProblem(nx, 1, nz, L, 0.0, np.ones(nx), **kw)
+    e1, e2 = _surfaces(nx, 1, 22)
+    b = _rhs(ora, nz, 23)
+    x = torch.zeros(gpu.m, dtype=torch.float64, device=DEV)
+    sw.test_stall_exchange(gpu.handle, 3)
+    gpu.solve(_t(e1), _t(e2), _t(b), x)
+    assert gpu.stats()["status"] == -6
+    xo, so, co = ora.solve(e1, e2, b)
+    gpu.solve(_t(e1), _t(e2), _t(b), x)
+    sg = gpu.stats()
+    assert sg["status"] == 0, sg
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
+    with pytest.raises(sw.SawaveError):
+        sw.test_stall_exchange(sw.Problem(nx, 1, nz, L, 0.0, np.ones(nx), executor="persistent").handle, 1)

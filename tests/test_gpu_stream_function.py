@@ -7,11 +7,13 @@ on the same Fenton initial condition.
 Tolerances: with solves to 1e-12 the fields agree to 1e-9 relative after
 every stage (as in test_gpu_parity.py).  With the paper's 1e-8 the fields agree
 to 1e-6 after the run, the previous-solution warm-up solves to +-2 iterations
-and the mean iteration count of the subspace-guess solves to 15 %.  Solve-by-solve counts are not compared on this run: they are chaotic
-in the rounding, as the oracle shows against itself (the same run with eta
-perturbed by 1e-10 relative changes single solves by up to 19 iterations and
-the mean by 4 %); the exact per-solve comparison on shared systems is the Airy
-trajectory test of test_gpu_parity.py.
+and the mean iteration count of the 90 subspace-guess solves to the band
+BAND_STREAM (25 %).  Solve-by-solve counts are not compared on this run: they
+are chaotic in the rounding.  The band comes from the oracle against itself
+(tests/test_sensitivity.py): with eta perturbed by 1e-13 relative, the same
+window's mean moved by up to 19 % (standard deviation 6-7 %) over 8 seeds.
+The per-solve comparisons on shared systems are in test_gpu_parity.py and
+test_gpu_iterations.py.
 """
 import math
 
@@ -20,6 +22,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from test_sensitivity import BAND_STREAM
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -86,7 +89,7 @@ def test_paper_subspace_run_iterations(sw, guess, executor):
     kw = dict(restart=20, max_restarts=100, tol=1e-8, guess=guess, k=10, decay=0.7, n_init_solves=30)
     if guess == "rrf":
         kw["history"] = 15
-    its = _run(sw, wl, 12, kw, executor, False, 1e-6)
+    its = _run(sw, wl, 24, kw, executor, False, 1e-6)
     assert np.all(np.abs(its[:30, 0] - its[:30, 1]) <= 2), its[:30].T     # previous-solution warm-up
     g, o = its[30:, 0].mean(), its[30:, 1].mean()
-    assert abs(g - o) <= 0.15 * o, (g, o, its[30:].T)
+    assert abs(g - o) <= BAND_STREAM * o, (g, o, its[30:].T)

@@ -3,10 +3,14 @@
 It serves callers that cannot call cudaMalloc (a memory budget or pool that
 forbids new device allocations, or a framework that owns every buffer): its
 scratch lives in a static device array of at most 65,536 columns.  Here it is
-called through the C ABI twice in a row, each time on new inputs, and compared
-with the regular entry point sw_apply_operator on the same inputs, with the
-element-wise bound the operator parity tests use: 1e-12 (|A| |x|).  Grids above
-the column limit are rejected before any GPU work.
+called through the C ABI twice in a row, each time on new inputs, and its
+output is compared with the regular entry point sw_apply_operator on the same
+inputs and with the oracle's assembled operator, A x, both with the
+element-wise bound the operator parity tests use: 1e-12 (|A| |x|).  The cases
+cover a 2-D bar, a 3-D field, the deepest sigma grid the entry point accepts
+(nz = 61, where the 3-D tile shrinks) and a grid exactly at the column limit
+(256 x 256 columns, where the scratch regions are full).  Grids above the
+limit are rejected before any GPU work.
 
 This file is named so that pytest collects it last.
 """
@@ -38,24 +42,20 @@ def test_rejects_grids_above_the_static_limit(sw):
     assert e.value.code == -1 and "65536" in str(e.value)
 
 
-def _bound(nx, ny, nz, lx, ly, h, e1, e2, x):
-    import oracle as O
-    ora = O.OracleProblem(nx, ny, nz, lx, ly, h)
-    ora.assemble(e1, e2)
-    A = ora.matrix()
-    return abs(A) @ np.abs(x)
-
-
 @pytest.mark.gpu
-@pytest.mark.parametrize("dims", [(64, 1, 9), (16, 8, 9)], ids=["2d_bar", "3d_bumps"])
-def test_matches_regular_apply_on_two_calls(sw, dims):
+@pytest.mark.parametrize("dims", [(64, 1, 9), (16, 8, 9), (16, 8, 61), (256, 256, 7)],
+                         ids=["2d_bar", "3d_bumps", "3d_nz61", "3d_at_limit"])
+def test_matches_regular_apply_and_oracle_on_two_calls(sw, dims):
+    import oracle as O
     nx, ny, nz = dims
     L = 2 * math.pi
+    ly = L if ny > 1 else 0.0
     X, Y = np.meshgrid(np.arange(nx) * (L / nx), np.arange(ny) * (L / ny), indexing="xy")
     h = (1.0 - 0.3 * np.exp(-2 * ((X - 3) ** 2 + (Y - 2) ** 2))).ravel()
     dev = torch.device("cuda")
-    grid = sw.Grid(nx, ny, nz, L, L if ny > 1 else 0.0)
-    prob = sw.Problem(nx, ny, nz, L, L if ny > 1 else 0.0, h)
+    grid = sw.Grid(nx, ny, nz, L, ly)
+    prob = sw.Problem(nx, ny, nz, L, ly, h)
+    ora = O.OracleProblem(nx, ny, nz, L, ly, h)
     m = prob.m
     rng = np.random.default_rng(21)
     dh = torch.tensor(h, device=dev)
@@ -69,7 +69,12 @@ def test_matches_regular_apply_on_two_calls(sw, dims):
         sw.apply_operator(prob.handle, te1, te2, tx, ref)
         sw.apply_operator_noalloc(grid, dh, te1, te2, tx, out)
         torch.cuda.synchronize()
-        diff = np.abs(out.cpu().numpy() - ref.cpu().numpy())
-        bound = _bound(nx, ny, nz, L, L if ny > 1 else 0.0, h, e1, e2, x)
-        assert np.all(diff <= 1e-12 * bound), (call, (diff / bound).max())
+        o = out.cpu().numpy()
+        ora.assemble(e1, e2)
+        A = ora.matrix()
+        bound = abs(A) @ np.abs(x)
+        d_reg = np.abs(o - ref.cpu().numpy())
+        d_ora = np.abs(o - A @ x)
+        assert np.all(d_reg <= 1e-12 * bound), (call, (d_reg / bound).max())
+        assert np.all(d_ora <= 1e-12 * bound), (call, (d_ora / bound).max())
     prob.close()
