@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-roofline-large", action="store_true")
+    ap.add_argument("--n3d-roof", type=int, default=512, help="roofline_large: nx = ny of the 3-D field")
     ap.add_argument("--members", type=int, default=512, help="batch512: number of instances")
     ap.add_argument("--clusters", default="1,4,8", help="batch512: thread blocks per member to measure")
     ap.add_argument("--spinup", type=int, default=800, help="flume2048: steps from rest before timing")
@@ -342,6 +344,7 @@ def gpu_arm(args, rank, world, local_rank):
     ph1 = sw.get_phase_times(P.handle)
     P.close()
     nsolves = 5 * args.steps
+    executor_used = {0: "auto", 1: "persistent", 2: "streamed", 3: "resident"}.get(s1.get("executor"), "?")
     value, total_ms = replica_value(total_ms, nsolves, world, dist, dev)
     its = (s1["total_iterations"] - s0["total_iterations"]) / nsolves
     mflops = s1["model_flops"] - s0["model_flops"]
@@ -416,8 +419,8 @@ def gpu_arm(args, rank, world, local_rank):
     fp64_peak = sm_count * 2 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
     achieved_tf = mflops / (solve_ms / 1e3) / 1e12 if solve_ms > 0 else None
     achieved_gbs = mbytes / (solve_ms / 1e3) / 1e9 if solve_ms > 0 else None
-    traffic = profile_traffic("solve_kernel")
-    roof = {"kernel": "solve_kernel", "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
+    traffic = profile_traffic("resident_kernel" if executor_used == "resident" else "solve_kernel")
+    roof = {"kernel": "resident_kernel" if executor_used == "resident" else "solve_kernel", "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
             "unit": "TFLOP/s", "frac": (achieved_tf / fp64_peak) if achieved_tf else None,
             "traffic": traffic, "peak_source": "FP64 2 FMA/clk/SM x %d SMs x %.0f MHz" % (sm_count, peaks.get("sm_max_mhz", 2070.0)),
             "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": peaks.get("hbm_gbs"),
@@ -438,6 +441,12 @@ def gpu_arm(args, rank, world, local_rank):
         cold["oracle_cold_start_iters"] = oracle_cold
     mixed_out = {k: mixed[k] for k in ("value", "iters_per_solve", "ms_per_solve")}
     mixed_out["error_vs_fp64_oracle"] = errs["mixed"]
+    roof_large = None
+    if not args.no_roofline_large:
+        try:
+            roof_large = roofline_large(sw, torch, dev, args.n3d_roof, peaks)
+        except sw.SawaveError as err:
+            roof_large = {"unavailable": str(err)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -448,15 +457,75 @@ def gpu_arm(args, rank, world, local_rank):
             "speedup_vs_previous": value / prev["value"] / world,
             "config": {"workload": WORKLOAD, "nx": 512, "nz": 17, "unknowns": wl["m"], "guess": "ewma", "k": args.k,
                        "decay": args.decay, "tol": 1e-8, "restart": 20, "n_init_steps": N_INIT_STEPS,
-                       "history_fill_steps_untimed": N_INIT_STEPS, "dt": wl["dt"],
+                       "history_fill_steps_untimed": N_INIT_STEPS, "dt": wl["dt"], "executor": executor_used,
                        "window": "every guess mode: %d untimed steps (history fill + warm-up), then the same %d "
                                  "timed steps" % (pre, args.steps),
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "roofline": roof, "roofline_large": roof_large, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches, "launches_per_solve": launches / nsolves, "wall_s_timed": wall,
             "phase_us_per_solve": {k: round((ph1[k] - ph0[k]) / nsolves, 2) for k in ph1}}
     print(json.dumps(line), flush=True)
+
+
+def roofline_large(sw, torch, dev, n3d, peaks):
+    """Per-kernel roofline of the streamed executor at a bandwidth size: the
+    3-D field (n3d x n3d x 17, bumps, 16 directional components) in the
+    precision form, two stage solves, then the hot kernels of an Arnoldi step
+    timed alone (sw_profile_kernels: CUDA events, L2 written between launches).
+    Algorithmic bytes and flops per launch follow the method's counts per point
+    (FP32 inner vectors and factors; m unknowns, ncol columns, P levels, s
+    factor slots per row, 84 of them off-column)."""
+    import workloads as W
+    wl = W.bumpy_3d(nx=n3d, ny=n3d)
+    t0 = time.perf_counter()
+    P = sw.Problem(wl["nx"], wl["ny"], wl["nz"], wl["lx"], wl["ly"], wl["h"], precision="mixed", executor="streamed",
+                   restart=20, max_restarts=500, tol=1e-8, guess="ewma", k=10, decay=0.9, n_init_solves=30, seed=2511)
+    create_s = time.perf_counter() - t0
+    sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+    t = lambda a: torch.tensor(a, device=dev)
+    sw.set_state(P.handle, t(wl["u"]), t(wl["v"]), t(wl["w"]), t(wl["eta"]))
+    for _ in range(2):
+        sw.advance_stage(P.handle)
+    torch.cuda.synchronize()
+    st = sw.get_stats(P.handle)
+    us = sw.profile_kernels(P.handle, reps=5)
+    col, tx, ty = sw.autotuned_apply(P.handle)
+    P.close()
+    m, ncol, Pl, s_slots, off = wl["m"], wl["nx"] * wl["ny"], wl["nz"] + 1, 91, 84
+    j = 10
+    model = {   # bytes, flops per launch (class of launches)
+        "apply": (8.0 * m + 4.0 * 16 * ncol, 123.0 * m, "alu"),
+        "ilu_gather_fwd": (4.0 * (off / 2) * m + 8.0 * m, 2.0 * (off / 2) * m, "hbm"),
+        "ilu_products": (2.0 * 4 * Pl * Pl * ncol + 16.0 * m, 4.0 * Pl * m, "hbm"),
+        "ilu_gather_bwd": (4.0 * (off / 2) * m + 6.0 * m, 2.0 * (off / 2) * m, "hbm"),
+        "cgs_pass1_j10": (4.0 * (j + 2) * m, 2.0 * (j + 1) * m, "hbm"),
+        "cgs_pass2_j10": (4.0 * (j + 3) * m, 4.0 * (j + 1) * m, "hbm"),
+        "cgs_pass3_j10": (4.0 * (j + 3) * m, 2.0 * (j + 1) * m + 2.0 * m, "hbm"),
+        "ilu_application": ((4.0 * (s_slots + 1) + 16.0) * m, (2.0 * s_slots - 1) * m, "hbm"),
+    }
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sm_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    hbm = peaks.get("hbm_gbs")
+    kern = {}
+    for k, v in us.items():
+        b, f, bound = model[k]
+        gbs = b / (v * 1e-6) / 1e9 if v > 0 else None
+        tfs = f / (v * 1e-6) / 1e12 if v > 0 else None
+        frac = (tfs / fp32_peak) if bound == "alu" else (gbs / hbm if hbm else None)
+        kern[k] = {"us_per_launch": v, "alg_bytes": b, "alg_flops": f, "gbs": gbs, "tflops": tfs, "bound": bound,
+                   "frac": frac}
+    dom = max((k for k in kern if k != "ilu_application"), key=lambda k: kern[k]["us_per_launch"])
+    return {"workload": "bumpy3d_%dx%dx17" % (n3d, n3d), "unknowns": m, "precision": "mixed (FP32 inner)",
+            "executor": "streamed", "create_s": create_s, "solves": 2, "iters_last_solve": st["iterations"],
+            "apply_form": {"column_marching": bool(col), "tile": [tx, ty]},
+            "peaks": {"hbm_gbs": hbm, "hbm_source": "measured copy (MEASURED_PEAKS.json)",
+                      "fp32_tflops": fp32_peak,
+                      "fp32_source": "unit counts: %d SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % (
+                          sm_count, peaks.get("sm_max_mhz", 2070.0))},
+            "kernels": kern, "dominant": dom,
+            "timing": "sw_profile_kernels: CUDA events on its own stream, 5 launches after one untimed, "
+                      "a 256 MiB buffer written before every launch (inputs from HBM)"}
 
 
 def _solve_errors(sw, torch, dev, wl, P, pre, steps):

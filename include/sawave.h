@@ -69,7 +69,9 @@ extern "C" {
 #define SW_PRECISION_FP64 0  /* every step in FP64 */
 #define SW_PRECISION_MIXED 1 /* FP32 inner GMRES cycles, FP64 outer residual */
 
-#define SW_EXEC_AUTO 0        /* persistent below SW_EXEC_STREAMED_MIN unknowns, streamed above */
+#define SW_EXEC_AUTO 0        /* resident where it applies (see SW_EXEC_RESIDENT) and the problem fits in
+                                 shared memory; else persistent below SW_EXEC_STREAMED_MIN unknowns,
+                                 streamed above */
 #define SW_EXEC_PERSISTENT 1  /* one cooperative kernel per solve, one block per SM: no host round
                                  trip inside a solve, lowest latency for small problems */
 #define SW_EXEC_STREAMED 2    /* one high-occupancy kernel per phase, small control kernels in
@@ -126,6 +128,7 @@ typedef struct {
     double model_flops;    /* algorithmic FP operations of all solves so far (cost model of the
                               operator, preconditioner, Gram-Schmidt and guess; not counters) */
     double model_bytes;    /* algorithmic bytes moved by all solves so far (same model) */
+    int executor;          /* SW_EXEC_* the solves run on (resolved from SW_EXEC_AUTO) */
 } sw_stats;
 
 typedef struct {
@@ -301,6 +304,28 @@ int sw_get_solve_time(sw_problem *p, double *total_ms, long long *n_timed);
  * 6 Arnoldi apply, 7 Arnoldi preconditioner, 8-10 the three Gram-Schmidt
  * passes, 11 Givens rotations, 12 solution update, 13 true residual. */
 int sw_get_phase_times(sw_problem *p, double *us, int n);
+
+/* Profiling aid for problems on the streamed executor, after at least one
+ * solve: the hot kernels of an Arnoldi step timed alone on the problem's own
+ * buffers with CUDA events on a private stream, `reps` launches each after
+ * one untimed launch, a 256 MiB buffer written before every launch so that
+ * inputs come from HBM (allocated and freed by the call).  us[i] (i < n <= 8)
+ * receives the mean duration in microseconds of: 0 the operator apply of the
+ * Arnoldi step (autotuned form), 1 the forward ILU gathers of every colour,
+ * 2 the in-column block products of both sweeps, 3 the backward ILU gathers,
+ * 4-6 the three Gram-Schmidt passes at Arnoldi index j = 10, 7 one whole ILU
+ * application.  The control state of the last solve is restored. */
+int sw_profile_kernels(sw_problem *p, int reps, double *us, int n);
+/* The operator form the streamed executor's autotuner picked: *column_form 1
+ * for the column-marching kernel (tile tile_x x tile_y columns), 0 for the
+ * staged tile kernel of tile_x x tile_y columns. */
+int sw_autotuned_apply(sw_problem *p, int *column_form, int *tile_x, int *tile_y);
+/* Override the autotuner's choice for the streamed executor's Arnoldi apply:
+ * 1 the column-marching kernel (periodic grids with 10, 18 or 34 levels, nx a
+ * multiple of 32 and ny of 8 in 3-D, nx a multiple of 256 in 2-D), 0 the
+ * staged tile kernel.  Same result up to rounding.  SW_ERR_BAD_ARG when the
+ * column form does not serve the grid or another executor runs the solves. */
+int sw_set_apply_form(sw_problem *p, int column_form);
 
 /* Testing aid for failure detection without a GPU fault: in the next solve of
  * a problem on the resident executor, block 0 stops raising its flag from its

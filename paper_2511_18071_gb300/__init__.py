@@ -15,7 +15,7 @@ __all__ = ["Grid", "Params", "Stats", "Physics", "Problem", "create_problem", "d
            "solve_poisson", "solve_poisson_host", "get_stats", "apply_operator", "apply_preconditioner",
            "subspace_guess", "apply_operator_noalloc", "get_sketch", "set_sketch", "draw_omega", "set_physics", "set_state", "get_state",
            "advance_stage", "set_relaxation", "set_step", "Relaxation", "create_batch", "destroy_batch", "batch_solve", "batch_advance_stage", "Batch",
-           "get_last_system", "get_phase_times", "enable_timing", "get_solve_time", "test_stall_exchange", "library_path", "SawaveError", "GUESS",
+           "get_last_system", "get_phase_times", "enable_timing", "get_solve_time", "test_stall_exchange", "profile_kernels", "autotuned_apply", "set_apply_form", "library_path", "SawaveError", "GUESS",
            "PRECISION", "EXECUTOR"]
 
 SW_OK = 0
@@ -52,7 +52,8 @@ class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int), ("status", C.c_int),
                 ("res0", C.c_double), ("res_final", C.c_double), ("true_res", C.c_double),
                 ("guess_res", C.c_double), ("n_solves", C.c_longlong), ("total_iterations", C.c_longlong),
-                ("launches", C.c_longlong), ("model_flops", C.c_double), ("model_bytes", C.c_double)]
+                ("launches", C.c_longlong), ("model_flops", C.c_double), ("model_bytes", C.c_double),
+                ("executor", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -108,6 +109,9 @@ def lib():
         L.sw_batch_set_cluster.argtypes = [vp, ip]
         L.sw_get_solve_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
         L.sw_test_stall_exchange.argtypes = [vp, ip]
+        L.sw_profile_kernels.argtypes = [vp, ip, vp, ip]
+        L.sw_autotuned_apply.argtypes = [vp, C.POINTER(ip), C.POINTER(ip), C.POINTER(ip)]
+        L.sw_set_apply_form.argtypes = [vp, ip]
         L.sw_last_error.restype = C.c_char_p
         for name in ["sw_create_problem", "sw_destroy_problem", "sw_problem_size", "sw_solve_poisson",
                      "sw_solve_poisson_host", "sw_get_stats", "sw_apply_operator", "sw_apply_preconditioner",
@@ -255,6 +259,30 @@ def set_relaxation(p, relax):
 
 def set_step(p, n_steps):
     return _check(lib().sw_set_step(p, int(n_steps)))
+
+
+PROFILED_KERNELS = ["apply", "ilu_gather_fwd", "ilu_products", "ilu_gather_bwd", "cgs_pass1_j10", "cgs_pass2_j10",
+                    "cgs_pass3_j10", "ilu_application"]
+
+
+def profile_kernels(p, reps=5):
+    """Mean microseconds per launch of the streamed executor's hot kernels (see sawave.h)."""
+    import numpy as np
+    out = np.zeros(len(PROFILED_KERNELS))
+    _check(lib().sw_profile_kernels(p, int(reps), C.c_void_p(out.ctypes.data), len(PROFILED_KERNELS)))
+    return dict(zip(PROFILED_KERNELS, out.tolist()))
+
+
+def autotuned_apply(p):
+    """(column_form, tile_x, tile_y) of the streamed executor's operator."""
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().sw_autotuned_apply(p, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def set_apply_form(p, column_form):
+    """Streamed executor: force the column-marching (1) or staged tile (0) operator."""
+    return _check(lib().sw_set_apply_form(p, int(bool(column_form))))
 
 
 def test_stall_exchange(p, exchange):

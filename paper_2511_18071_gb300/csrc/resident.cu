@@ -17,12 +17,17 @@
 //  - the operator and the ILU colour sweeps couple a column only to columns at
 //    most three away, i.e. to the two neighbouring blocks: before every sweep
 //    and apply that needs them, a block publishes its three leftmost and three
-//    rightmost columns in a mailbox in global memory, raises its sequence flag
-//    and waits for its two neighbours' flags, instead of a grid barrier;
-//  - inner products are all-reduced: every block writes its partial sums,
-//    counts itself in with one atomic, waits until every block has, and sums
-//    the partials in a fixed order (so every block holds bit-identical values
-//    and takes the same decisions);
+//    rightmost columns in a mailbox in global memory and reads its two
+//    neighbours' mailboxes, instead of a grid barrier;
+//  - inner products are all-reduced: every block publishes its partial sums
+//    and sums every block's partials in a fixed order (so every block holds
+//    bit-identical values and takes the same decisions);
+//  - mailbox and partial-sum words are self-validating: each 8-byte word holds
+//    32 bits of data and a 32-bit tag (launch epoch and exchange or reduction
+//    number), written and read as single 8-byte accesses, so a reader polls
+//    the data itself until its tag appears (one round trip through L2 once the
+//    data have landed; no fence, flag or counter); slots alternate between two
+//    buffers, and a block cannot get two exchanges ahead of its neighbours;
 //  - the Gram-Schmidt step takes two all-reduces instead of three: the second
 //    pass returns the projections and ||w||^2 together, and the norm of the
 //    twice-orthogonalised vector is ||w||^2 - ||h'||^2 (V orthonormal), with a
@@ -44,12 +49,28 @@ constexpr unsigned long long R_WAIT_NS = 2000000000ull;   // 2 s
 // Device description of the resident layout of one problem.
 struct ResDev {
     int C, NB, nl, nlp, mv, blob, noff;
-    int stall;             // testing aid: from this exchange on, block 0 withholds its flag (-1: never)
+    int stall;             // testing aid: from this exchange on, block 0 publishes nothing (-1: never)
+    unsigned epoch;        // launch epoch, 1..4095, in the high bits of every tag
     const double *cblob;   // NB x blob: off-column factors fac[i][l][cx], then Linv and Uinv of the block's columns
-    double *mail;          // 2 x NB x mv x P x 6 boundary columns
-    unsigned *sync;        // [0] all-reduce arrivals, [1] abort, [2 + b] exchange flag of block b
-    double *part;          // 2 x NB x PART_STRIDE partial sums
+    unsigned long long *mail;   // 2 x NB x mv x P x 6 boundary values, two tagged words each
+    unsigned *sync;             // [0] abort flag
+    unsigned long long *part;   // 2 x NB x PART_STRIDE partial sums, two tagged words each
 };
+
+__device__ __forceinline__ void r_st64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long r_ld64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+// A double as two tagged words: (tag << 32) | low 32 bits, (tag << 32) | high 32 bits.
+__device__ __forceinline__ void r_put(unsigned long long *p, double v, unsigned tag) {
+    const unsigned long long t = (unsigned long long)tag << 32;
+    r_st64(p, t | (unsigned)__double2loint(v));
+    r_st64(p + 1, t | (unsigned)__double2hiint(v));
+}
 
 __device__ __forceinline__ unsigned r_ld_acquire(const unsigned *p) {
     unsigned v;
@@ -57,13 +78,30 @@ __device__ __forceinline__ unsigned r_ld_acquire(const unsigned *p) {
     return v;
 }
 
-// Wait until *a >= target and *b >= target (thread 0 only).  False when the
-// bound runs out (the abort flag is then raised) or another block aborted.
-__device__ inline bool r_wait_ge(const unsigned *a, const unsigned *b, unsigned target, unsigned *abortp) {
-    const unsigned long long t0 = global_ns();
-    for (unsigned it = 1;; ++it) {
-        if (r_ld_acquire(a) >= target && r_ld_acquire(b) >= target) return true;
-        if ((it & 31) == 0) {
+// Up to N tagged doubles at addr(0..n-1): every round loads all words still
+// missing their tag at once (one round trip per round), until all carry it.
+template <int N, class Addr>
+__device__ __forceinline__ bool r_get_n(Addr addr, int n, unsigned tag, unsigned *abortp, double (&out)[N]) {
+    unsigned long long lo[N], hi[N];
+    unsigned missing = n >= 32 ? 0xffffffffu : (1u << n) - 1u;
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            if (missing & (1u << q)) {
+                lo[q] = r_ld64(addr(q));
+                hi[q] = r_ld64(addr(q) + 1);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+            if ((missing & (1u << q)) && (unsigned)(lo[q] >> 32) == tag && (unsigned)(hi[q] >> 32) == tag) {
+                out[q] = __hiloint2double((int)(unsigned)hi[q], (int)(unsigned)lo[q]);
+                missing &= ~(1u << q);
+            }
+        if (!missing) return true;
+        if (it == 0) t0 = global_ns();
+        if ((it & 31) == 31) {
             if (r_ld_acquire(abortp)) return false;
             if (global_ns() - t0 > R_WAIT_NS) {
                 atomicExch(abortp, 1u);
@@ -73,10 +111,10 @@ __device__ inline bool r_wait_ge(const unsigned *a, const unsigned *b, unsigned 
     }
 }
 
-// Per-block view of the solve's shared memory and synchronisation state.
+// Per-block view of the solve's shared memory (set once, then read-only; kept
+// in shared memory itself to leave registers to the arithmetic).
 struct RCtx {
     int b, bl, br, C, P, nl, nlp, HX, NB;
-    unsigned seq, round;
     double *fac, *linv, *uinv;          // constants
     double *V, *t, *x, *bb, *r, *xp;    // vectors (nlp stride between Krylov vectors)
     double *Y, *Wm, *halo, *sp, *sq, *cc, *ws1, *ws2;
@@ -88,68 +126,89 @@ struct RCtx {
 // Publish the three leftmost and three rightmost columns of nv local vectors
 // (vector c at vec + c * stride) and fill halo[c][l][0..5] with the left
 // neighbour's three rightmost and the right neighbour's three leftmost columns.
-__device__ bool r_exchange(RCtx &X, const ResDev &R, SmemFixed &S, const double *vec, int stride, int nv) {
+// Publication and collection may be separated by other work (the collection
+// of exchange seq must come before the publication of exchange seq + 1).
+__device__ __noinline__ void r_publish(const RCtx &X, const ResDev &R, const double *vec, int stride, int nv,
+                                       unsigned seq) {
     const int P = X.P, C = X.C, n6 = P * 6;
-    X.seq++;
-    const int par = X.seq & 1;
-    double *mine = R.mail + ((size_t)(par * X.NB + X.b) * R.mv) * n6;
-    for (int i = threadIdx.x; i < nv * n6; i += NTHREADS) {
-        const int c = i / n6, rr = i - c * n6, l = rr / 6, e = rr - l * 6;
-        mine[i] = vec[(size_t)c * stride + l * C + (e < 3 ? e : C - 6 + e)];
+    const unsigned tag = (R.epoch << 20) | seq;
+    const int par = seq & 1;
+    unsigned long long *mine = R.mail + 2 * ((size_t)(par * X.NB + X.b) * R.mv) * n6;
+    if (!(X.b == 0 && R.stall > 0 && (int)seq >= R.stall)) {
+        for (int i = threadIdx.x; i < nv * n6; i += NTHREADS) {
+            const int c = i / n6, rr = i - c * n6, l = rr / 6, e = rr - l * 6;
+            r_put(mine + 2 * i, vec[(size_t)c * stride + l * C + (e < 3 ? e : C - 6 + e)], tag);
+        }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (!(X.b == 0 && R.stall > 0 && (int)X.seq >= R.stall)) atomicExch(R.sync + 2 + X.b, X.seq);
-        S.flags[7] = r_wait_ge(R.sync + 2 + X.bl, R.sync + 2 + X.br, X.seq, R.sync + 1) ? 1 : 0;
+}
+
+__device__ __noinline__ bool r_collect(const RCtx &X, const ResDev &R, int nv, unsigned seq) {
+    const int P = X.P, n6 = P * 6;
+    const unsigned tag = (R.epoch << 20) | seq;
+    const int par = seq & 1;
+    const unsigned long long *ml = R.mail + 2 * ((size_t)(par * X.NB + X.bl) * R.mv) * n6;
+    const unsigned long long *mr = R.mail + 2 * ((size_t)(par * X.NB + X.br) * R.mv) * n6;
+    bool ok = true;
+    constexpr int CH = 8;
+    for (int i0 = threadIdx.x; i0 < nv * n6 && ok; i0 += CH * NTHREADS) {
+        const int cnt = min(CH, (nv * n6 - i0 + NTHREADS - 1) / NTHREADS);
+        double v[CH];
+        ok = r_get_n<CH>([&](int q) {
+            const int i = i0 + q * NTHREADS;
+            return i % 6 < 3 ? ml + 2 * (i + 3) : mr + 2 * (i - 3);
+        }, cnt, tag, R.sync, v);
+#pragma unroll
+        for (int q = 0; q < CH; ++q)
+            if (q < cnt) X.halo[i0 + q * NTHREADS] = v[q];
     }
-    __syncthreads();
-    if (!S.flags[7]) return false;
-    const double *ml = R.mail + ((size_t)(par * X.NB + X.bl) * R.mv) * n6;
-    const double *mr = R.mail + ((size_t)(par * X.NB + X.br) * R.mv) * n6;
-    for (int i = threadIdx.x; i < nv * n6; i += NTHREADS) {
-        const int e = i % 6;
-        X.halo[i] = e < 3 ? __ldcg(ml + i + 3) : __ldcg(mr + i - 3);
-    }
-    __syncthreads();
-    return true;
+    return __syncthreads_and(ok) != 0;
+}
+
+__device__ bool r_exchange(const RCtx &X, const ResDev &R, const double *vec, int stride, int nv, unsigned seq) {
+    r_publish(X, R, vec, stride, nv, seq);
+    return r_collect(X, R, nv, seq);
 }
 
 // ---- all-reduce of block partial sums ----------------------------------------
 
 // out[v] = sum over blocks of bp[v] (v < nv <= PART_STRIDE), summed in the same
 // order by every block.  bp is in shared memory; out may be S.res.
-__device__ bool r_allreduce(RCtx &X, const ResDev &R, SmemFixed &S, const double *bp, int nv, double *out) {
-    const int par = X.round & 1;
-    double *mine = R.part + (size_t)(par * X.NB + X.b) * PART_STRIDE;
-    for (int i = threadIdx.x; i < nv; i += NTHREADS) mine[i] = bp[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(R.sync, 1u);
-        const unsigned target = (X.round + 1) * (unsigned)X.NB;
-        S.flags[7] = r_wait_ge(R.sync, R.sync, target, R.sync + 1) ? 1 : 0;
-    }
-    X.round++;
-    __syncthreads();
-    if (!S.flags[7]) return false;
-    const double *pp = R.part + (size_t)par * X.NB * PART_STRIDE;
+__device__ __noinline__ bool r_allreduce(const RCtx &X, const ResDev &R, SmemFixed &S, const double *bp, int nv,
+                                         double *out, unsigned round) {
+    const unsigned tag = (R.epoch << 20) | (0x80000u + round);
+    const int par = round & 1;
+    unsigned long long *mine = R.part + 2 * (size_t)(par * X.NB + X.b) * PART_STRIDE;
+    for (int i = threadIdx.x; i < nv; i += NTHREADS) r_put(mine + 2 * i, bp[i], tag);
+    const unsigned long long *pp = R.part + 2 * (size_t)par * X.NB * PART_STRIDE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool ok = true;
     for (int v0 = 0; v0 < nv; v0 += 32) {
         const int v = v0 + lane;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        if (v < nv) {
-            int bq = warp;
-            for (; bq + 3 * NWARPS < X.NB; bq += 4 * NWARPS) {
-                a0 += __ldcg(pp + (size_t)bq * PART_STRIDE + v);
-                a1 += __ldcg(pp + (size_t)(bq + NWARPS) * PART_STRIDE + v);
-                a2 += __ldcg(pp + (size_t)(bq + 2 * NWARPS) * PART_STRIDE + v);
-                a3 += __ldcg(pp + (size_t)(bq + 3 * NWARPS) * PART_STRIDE + v);
+        if (v < nv && ok) {
+            // blocks warp, warp + 8, ...: at most 20 (NB <= 160), loaded together
+            const int nmine = (X.NB - warp + NWARPS - 1) / NWARPS;
+            constexpr int CH = 20;
+            for (int u0 = 0; u0 < nmine && ok; u0 += CH) {
+                double t[CH];
+                const int cnt = min(CH, nmine - u0);
+                ok = r_get_n<CH>([&](int q) {
+                    return pp + 2 * ((size_t)(warp + NWARPS * (u0 + q)) * PART_STRIDE + v);
+                }, cnt, tag, R.sync, t);
+#pragma unroll
+                for (int q = 0; q < CH; ++q) {
+                    if (q >= cnt) break;
+                    // block warp + 8u goes to accumulator u mod 4 (a fixed order)
+                    const int u = u0 + q;
+                    if ((u & 3) == 0) a0 += t[q];
+                    else if ((u & 3) == 1) a1 += t[q];
+                    else if ((u & 3) == 2) a2 += t[q];
+                    else a3 += t[q];
+                }
             }
-            for (; bq < X.NB; bq += NWARPS) a0 += __ldcg(pp + (size_t)bq * PART_STRIDE + v);
         }
         S.red[warp * 32 + lane] = (a0 + a1) + (a2 + a3);
-        __syncthreads();
+        if (!__syncthreads_and(ok)) return false;
         if (warp == 0 && v < nv) {
             double s = 0.0;
 #pragma unroll
@@ -363,22 +422,110 @@ __device__ void r_bwd(const RCtx &X, double *out) {
     __syncthreads();
 }
 
+// One colour phase with the work of each column spread over several warps
+// (levels one per lane, P <= 32): the warps of a column take every nwc-th
+// off-column slot, then a slice of the rows of the column's inverse block,
+// and the slices are added; the warps' partial sums meet in shared memory.
+// Forward: out = Linv (in - lower couplings), then with UP the backward step
+// of the same colour, out = Uinv out; backward: out = Uinv (out - upper couplings).
+template <int L, int CC, bool FWD, bool UP>
+__device__ void r_phase(const RCtx &X, SmemFixed &S, const double *in, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int P = X.P, C = X.C;
+    const int ncc = C >> 2;                   // columns of this colour in the block (1..4)
+    const int nwc = ncc > 2 ? 2 : 4;          // warps per column
+    const int cs = warp / nwc, part = warp - cs * nwc;
+    const bool act = cs < ncc;
+    const int cx = 4 * cs + CC;
+    double *po = S.red, *py = S.xchg;
+    // off-column couplings, slots part, part + nwc, ...
+    double o = 0.0;
+    if (act && lane < P) {
+#pragma unroll
+        for (int i = 0; i < Off<L>::N; ++i) {
+            const int ox = Off<L>::ox(i);
+            const int nc = (CC + ox) & 3;
+            if (FWD ? (nc >= CC) : (nc <= CC)) continue;
+            if (i % nwc != part) continue;
+            const int lev = Off<L>::kk(i) < 0 ? lane : X.win[lane] + 1 + Off<L>::kk(i);
+            o += X.fac[((size_t)i * P + lane) * C + cx] * r_ext(X, out, X.halo, lev, cx + ox);
+        }
+    }
+    po[warp * 32 + lane] = o;
+    __syncthreads();
+    double g = 0.0;
+    if (act && lane < P) {
+        double os = 0.0;
+        for (int p = 0; p < nwc; ++p) os += po[(cs * nwc + p) * 32 + lane];
+        g = (FWD ? in[lane * C + cx] : out[lane * C + cx]) - os;
+    }
+    const int rng = (P + nwc - 1) / nwc, a0 = part * rng, a1 = min(P, a0 + rng);
+    const double *B = (FWD ? X.linv : X.uinv) + (size_t)(act ? cx : 0) * P * P;
+    double y = 0.0;
+    for (int a2 = a0; a2 < a1; ++a2) {
+        const double ga = __shfl_sync(0xffffffffu, g, a2);
+        if (act && lane < P) y += B[a2 * P + lane] * ga;
+    }
+    py[warp * 32 + lane] = y;
+    __syncthreads();
+    if (UP) {
+        // backward step of the last colour on the forward result
+        double yf = 0.0;
+        if (act && lane < P)
+            for (int p = 0; p < nwc; ++p) yf += py[(cs * nwc + p) * 32 + lane];
+        const double *U = X.uinv + (size_t)(act ? cx : 0) * P * P;
+        double z = 0.0;
+        for (int a2 = a0; a2 < a1; ++a2) {
+            const double ga = __shfl_sync(0xffffffffu, yf, a2);
+            if (act && lane < P) z += U[a2 * P + lane] * ga;
+        }
+        po[warp * 32 + lane] = z;
+        __syncthreads();
+        if (act && part == 0 && lane < P) {
+            double zs = 0.0;
+            for (int p = 0; p < nwc; ++p) zs += po[(cs * nwc + p) * 32 + lane];
+            out[lane * C + cx] = zs;
+        }
+    } else if (act && part == 0 && lane < P) {
+        double ys = 0.0;
+        for (int p = 0; p < nwc; ++p) ys += py[(cs * nwc + p) * 32 + lane];
+        out[lane * C + cx] = ys;
+    }
+    __syncthreads();
+}
+
 // out = U^-1 L^-1 in: four forward colours, four backward colours (the last
 // forward and first backward colour together), six boundary exchanges.
 template <int L>
-__device__ bool r_ilu(RCtx &X, const ResDev &R, SmemFixed &S, const double *in, double *out) {
+__device__ bool r_ilu(const RCtx &X, const ResDev &R, SmemFixed &S, const double *in, double *out, unsigned &seq) {
+    if (X.P <= 32) {
+        r_phase<L, 0, true, false>(X, S, in, out);
+        if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
+        r_phase<L, 1, true, false>(X, S, in, out);
+        if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
+        r_phase<L, 2, true, false>(X, S, in, out);
+        if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
+        r_phase<L, 3, true, true>(X, S, in, out);
+        if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
+        r_phase<L, 2, false, false>(X, S, in, out);
+        if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
+        r_phase<L, 1, false, false>(X, S, in, out);
+        if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
+        r_phase<L, 0, false, false>(X, S, in, out);
+        return true;
+    }
     r_fwd<L, 0, false>(X, in, out);
-    if (!r_exchange(X, R, S, out, 0, 1)) return false;
+    if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
     r_fwd<L, 1, false>(X, in, out);
-    if (!r_exchange(X, R, S, out, 0, 1)) return false;
+    if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
     r_fwd<L, 2, false>(X, in, out);
-    if (!r_exchange(X, R, S, out, 0, 1)) return false;
+    if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
     r_fwd<L, 3, true>(X, in, out);
-    if (!r_exchange(X, R, S, out, 0, 1)) return false;
+    if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
     r_bwd<L, 2>(X, out);
-    if (!r_exchange(X, R, S, out, 0, 1)) return false;
+    if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
     r_bwd<L, 1>(X, out);
-    if (!r_exchange(X, R, S, out, 0, 1)) return false;
+    if (!r_exchange(X, R, out, 0, 1, ++seq)) return false;
     r_bwd<L, 0>(X, out);
     return true;
 }
@@ -392,40 +539,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
     double *base = reinterpret_cast<double *>(smem_raw + ((sizeof(SmemFixed) + 255) & ~size_t(255)));
     const int tid = threadIdx.x;
     const int k = A.k, mr = A.restart;
-    RCtx X;
-    X.b = blockIdx.x;
-    X.NB = R.NB;
-    X.bl = X.b == 0 ? R.NB - 1 : X.b - 1;
-    X.br = X.b == R.NB - 1 ? 0 : X.b + 1;
-    X.C = R.C;
-    X.P = D.P;
-    X.nl = R.nl;
-    X.nlp = R.nlp;
-    X.HX = R.C + 2 * HALF;
-    X.seq = 0;
-    X.round = 0;
+    __shared__ RCtx Xs;
+    if (tid == 0) {
+        RCtx &X0 = Xs;
+        X0.b = blockIdx.x;
+        X0.NB = R.NB;
+        X0.bl = X0.b == 0 ? R.NB - 1 : X0.b - 1;
+        X0.br = X0.b == R.NB - 1 ? 0 : X0.b + 1;
+        X0.C = R.C;
+        X0.P = D.P;
+        X0.nl = R.nl;
+        X0.nlp = R.nlp;
+        X0.HX = R.C + 2 * HALF;
+        // shared-memory carve-out (doubles)
+        const int C0 = X0.C, P0 = X0.P, nl0 = X0.nl, nlp0 = X0.nlp;
+        double *q = base;
+        X0.fac = q; q += (size_t)R.noff * nl0;
+        X0.linv = q; q += (size_t)C0 * P0 * P0;
+        X0.uinv = q; q += (size_t)C0 * P0 * P0;
+        X0.V = q; q += (size_t)(mr + 1) * nlp0;
+        X0.t = q; q += nlp0;
+        X0.x = q; q += nlp0;
+        X0.bb = q; q += nlp0;
+        X0.r = q; q += nlp0;
+        X0.xp = q; q += nlp0;
+        X0.Y = q; q += (size_t)k * nl0;
+        X0.Wm = q; q += (size_t)k * nl0;
+        X0.halo = q; q += (size_t)R.mv * P0 * 6;
+        X0.sp = q; q += (size_t)P0 * X0.HX;
+        X0.sq = q; q += (size_t)P0 * X0.HX;
+        X0.cc = q; q += (size_t)NCC * C0;
+        X0.ws1 = q; q += (size_t)P0 * W;
+        X0.ws2 = q; q += (size_t)P0 * W;
+        X0.win = reinterpret_cast<int *>(q);
+    }
+    __syncthreads();
+    const RCtx &X = Xs;
+    unsigned seq = 0, round = 0;   // exchanges and reductions so far (the same in every block)
     const int C = X.C, P = X.P, nl = X.nl, nlp = X.nlp;
-    const int noff = R.noff;
-    // shared-memory carve-out (doubles)
-    double *q = base;
-    X.fac = q; q += (size_t)noff * nl;
-    X.linv = q; q += (size_t)C * P * P;
-    X.uinv = q; q += (size_t)C * P * P;
-    X.V = q; q += (size_t)(mr + 1) * nlp;
-    X.t = q; q += nlp;
-    X.x = q; q += nlp;
-    X.bb = q; q += nlp;
-    X.r = q; q += nlp;
-    X.xp = q; q += nlp;
-    X.Y = q; q += (size_t)k * nl;
-    X.Wm = q; q += (size_t)k * nl;
-    X.halo = q; q += (size_t)R.mv * P * 6;
-    X.sp = q; q += (size_t)P * X.HX;
-    X.sq = q; q += (size_t)P * X.HX;
-    X.cc = q; q += (size_t)NCC * C;
-    X.ws1 = q; q += (size_t)P * W;
-    X.ws2 = q; q += (size_t)P * W;
-    X.win = reinterpret_cast<int *>(q);
     double *bp = S.xchg;   // block partial sums
     const long long col0 = (long long)X.b * C;
     const long long m = D.m;
@@ -478,9 +629,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
 #define R_TRY(expr) do { if (!(expr)) goto aborted; } while (0)
 
     // reference norms ||b|| and ||M^-1 b||
-    R_TRY(r_ilu<L>(X, R, S, X.bb, X.t));
+    R_TRY(r_ilu<L>(X, R, S, X.bb, X.t, seq));
     r_block_sums(X, S, 2, [&](int p, double (&v)[4]) { v[0] += X.bb[p] * X.bb[p]; v[1] += X.t[p] * X.t[p]; }, bp);
-    R_TRY(r_allreduce(X, R, S, bp, 2, S.res));
+    R_TRY(r_allreduce(X, R, S, bp, 2, S.res, ++round));
     braw = sqrt(S.res[0]);
     bnorm = sqrt(S.res[1]);
     cost(A.cm.fM + 4.0, A.cm.bM + 8.0);
@@ -523,7 +674,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
         if (sub) {
             // W = A Y in FP64 (a8): one exchange for all k columns, then k applies
             cost(k * A.cm.fA, k * (A.cm.bA + 8.0));
-            R_TRY(r_exchange(X, R, S, X.Y, nl, k));
+            R_TRY(r_exchange(X, R, X.Y, nl, k, ++seq));
             for (int c = 0; c < k; ++c)
                 r_apply(X, D, X.Y + (size_t)c * nl, X.halo + (size_t)c * P * 6, 1.0, X.Wm + (size_t)c * nl, false);
         }
@@ -552,7 +703,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
             };
             cost(2.0 * nv, (k + 1.0) * 8.0);
             gram();
-            R_TRY(r_allreduce(X, R, S, bp, nv, S.res));
+            R_TRY(r_allreduce(X, R, S, bp, nv, S.res, ++round));
             if (tid < 32) {
                 for (int e = tid; e < ng; e += 32) {
                     S.G[S.ga[e] * k + S.gb[e]] = S.res[e];
@@ -595,7 +746,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
                 }
                 __syncthreads();
                 gram();
-                R_TRY(r_allreduce(X, R, S, bp, nv, S.res));
+                R_TRY(r_allreduce(X, R, S, bp, nv, S.res, ++round));
                 if (tid < 32) {
                     for (int e = tid; e < ng; e += 32) {
                         S.G[S.ga[e] * k + S.gb[e]] = S.res[e];
@@ -668,10 +819,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
     } else {
         for (int cycle = 0;; ++cycle) {
             // r = b - A x (FP64); V0 = M^-1 r
-            R_TRY(r_exchange(X, R, S, X.x, 0, 1));
+            R_TRY(r_exchange(X, R, X.x, 0, 1, ++seq));
             const double racc = r_apply(X, D, X.x, X.halo, 1.0, X.r, true);
             tick(PH_RES_APPLY);
-            R_TRY(r_ilu<L>(X, R, S, X.r, X.V));
+            R_TRY(r_ilu<L>(X, R, S, X.r, X.V, seq));
             {
                 double rsum = racc;
 #pragma unroll
@@ -691,7 +842,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
                 }
                 __syncthreads();
             }
-            R_TRY(r_allreduce(X, R, S, bp, 2, S.res));
+            R_TRY(r_allreduce(X, R, S, bp, 2, S.res, ++round));
             tick(PH_RES_ILU);
             const double beta = sqrt(S.res[1]);
             cost(A.cm.fA + A.cm.fM + 4.0, A.cm.bA + A.cm.bM + 8.0);
@@ -715,15 +866,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
             for (int j = 0; j < mr; ++j) {
                 double *w = X.V + (size_t)(j + 1) * nlp;
                 const double *vj = X.V + (size_t)j * nlp;
-                // w = M^-1 A v_j  (v_j = scale_j V_j)
-                R_TRY(r_exchange(X, R, S, vj, 0, 1));
+                // w = M^-1 A v_j  (v_j = scale_j V_j); the boundary of V_j was
+                // published when it was formed (V_0 here, the others after pass 3)
+                if (j == 0) r_publish(X, R, vj, 0, 1, ++seq);
+                R_TRY(r_collect(X, R, 1, seq));
                 r_apply(X, D, vj, X.halo, S.scale[j], X.t, false);
                 tick(PH_ARN_APPLY);
-                R_TRY(r_ilu<L>(X, R, S, X.t, w));
+                R_TRY(r_ilu<L>(X, R, S, X.t, w, seq));
                 tick(PH_ARN_ILU);
                 // Gram-Schmidt pass 1: d_i = V_i . w
                 r_block_dots(X, S, j + 1, w, false, bp);
-                R_TRY(r_allreduce(X, R, S, bp, j + 1, S.res));
+                R_TRY(r_allreduce(X, R, S, bp, j + 1, S.res, ++round));
                 tick(PH_CGS1);
                 if (tid < MAX_RESTART) {
                     const int i = tid;
@@ -740,7 +893,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
                 }
                 __syncthreads();
                 r_block_dots(X, S, j + 1, w, true, bp);
-                R_TRY(r_allreduce(X, R, S, bp, j + 2, S.res));
+                R_TRY(r_allreduce(X, R, S, bp, j + 2, S.res, ++round));
                 tick(PH_CGS2);
                 double hn2;
                 {
@@ -766,10 +919,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
                     w[p] = wv;
                 }
                 __syncthreads();
+                // the next apply's boundary exchange, in flight during the rotations
+                // (w is final now; its scale comes with the apply)
+                r_publish(X, R, w, 0, 1, ++seq);
                 // ||w||^2 - ||h'||^2 has lost accuracy when it is far below ||w||^2: reduce directly
                 if (!(hn2 > 1e-4 * S.res[j + 1])) {
                     r_block_sums(X, S, 1, [&](int p, double (&v)[4]) { v[0] += w[p] * w[p]; }, bp);
-                    R_TRY(r_allreduce(X, R, S, bp, 1, S.res));
+                    R_TRY(r_allreduce(X, R, S, bp, 1, S.res, ++round));
                     hn2 = S.res[0];
                 }
                 tick(PH_CGS3);
@@ -777,16 +933,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
                 if (tid == 0) {
                     const double hn = sqrt(fmax(hn2, 0.0));
                     S.scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+                    // the earlier rotations on the new column: row i + 1 as
+                    // rotated so far is the only carried value, one fused
+                    // multiply-add per rotation on the dependent chain
                     double *Hc = S.H;
+                    double tr = Hc[j];
                     for (int i = 0; i < j; ++i) {
-                        const double a = Hc[i * MAX_RESTART + j], bq = Hc[(i + 1) * MAX_RESTART + j];
-                        Hc[i * MAX_RESTART + j] = S.cs[i] * a + S.sn[i] * bq;
-                        Hc[(i + 1) * MAX_RESTART + j] = -S.sn[i] * a + S.cs[i] * bq;
+                        const double h1 = Hc[(i + 1) * MAX_RESTART + j], ci = S.cs[i], si = S.sn[i];
+                        const double ch = ci * h1;
+                        Hc[i * MAX_RESTART + j] = fma(ci, tr, si * h1);
+                        tr = fma(-si, tr, ch);
                     }
-                    const double a = Hc[j * MAX_RESTART + j];
-                    const double den = hypot(a, hn);
-                    S.cs[j] = a / den;
-                    S.sn[j] = hn / den;
+                    const double a = tr;
+                    const double den = sqrt(fma(a, a, hn * hn));
+                    const double rden = 1.0 / den;
+                    S.cs[j] = a * rden;
+                    S.sn[j] = hn * rden;
                     Hc[j * MAX_RESTART + j] = den;
                     S.g[j + 1] = -S.sn[j] * S.g[j];
                     S.g[j] = S.cs[j] * S.g[j];
@@ -822,7 +984,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
     }
     // true residual ||b - A x|| / ||b||; the solution is kept for the next guess
     {
-        R_TRY(r_exchange(X, R, S, X.x, 0, 1));
+        R_TRY(r_exchange(X, R, X.x, 0, 1, ++seq));
         const double racc = r_apply(X, D, X.x, X.halo, 1.0, X.r, true);
         double rsum = racc;
 #pragma unroll
@@ -841,7 +1003,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) resident_kernel(Dev D, SolveArgs 
             bp[0] = sv;
         }
         __syncthreads();
-        R_TRY(r_allreduce(X, R, S, bp, 1, S.res));
+        R_TRY(r_allreduce(X, R, S, bp, 1, S.res, ++round));
         true_res = braw > 0.0 ? sqrt(S.res[0]) / braw : sqrt(S.res[0]);
         cost(A.cm.fA + 3.0, A.cm.bA + 24.0);
     }
@@ -906,6 +1068,7 @@ struct Resident {
     ResDev R{};
     size_t smem = 0;
     const void *kern = nullptr;
+    unsigned epoch = 0;   // launches so far (the tag epoch is 1 + epoch mod 4095)
 };
 
 static size_t resident_smem(const Dev &D, int C, int mr, int k, int noff) {
@@ -964,12 +1127,17 @@ int setup_resident(Problem *P) {
     R.mv = P->params.k > 1 ? P->params.k : 1;
     R.noff = D.layout == BOX2D ? Off<BOX2D>::N : Off<CROSS2D>::N;
     R.blob = R.noff * R.nl + 2 * C * D.P * D.P;
-    double *blob = nullptr, *mail = nullptr, *part = nullptr;
+    double *blob = nullptr;
+    unsigned long long *mail = nullptr, *part = nullptr;
     unsigned *sync = nullptr;
+    const size_t mail_bytes = 2 * 2 * (size_t)R.NB * R.mv * D.P * 6 * sizeof(unsigned long long);
+    const size_t part_bytes = 2 * 2 * (size_t)R.NB * PART_STRIDE * sizeof(unsigned long long);
     e = cudaMalloc((void **)&blob, (size_t)R.NB * R.blob * sizeof(double));
-    if (e == cudaSuccess) { P->allocs.push_back(blob); e = cudaMalloc((void **)&mail, 2 * (size_t)R.NB * R.mv * D.P * 6 * sizeof(double)); }
-    if (e == cudaSuccess) { P->allocs.push_back(mail); e = cudaMalloc((void **)&part, 2 * (size_t)R.NB * PART_STRIDE * sizeof(double)); }
-    if (e == cudaSuccess) { P->allocs.push_back(part); e = cudaMalloc((void **)&sync, (2 + (size_t)R.NB) * sizeof(unsigned)); }
+    if (e == cudaSuccess) { P->allocs.push_back(blob); e = cudaMalloc((void **)&mail, mail_bytes); }
+    if (e == cudaSuccess) { P->allocs.push_back(mail); e = cudaMemset(mail, 0, mail_bytes); }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&part, part_bytes);
+    if (e == cudaSuccess) { P->allocs.push_back(part); e = cudaMemset(part, 0, part_bytes); }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sync, sizeof(unsigned));
     if (e == cudaSuccess) P->allocs.push_back(sync);
     if (e != cudaSuccess) return cuda_fail(e, "resident executor set-up");
     R.cblob = blob;
@@ -1003,7 +1171,10 @@ int solve_resident(Problem *P, const SolveArgs &A, cudaStream_t s) {
     ResDev R = Rs->R;
     R.stall = P->resident_stall;
     P->resident_stall = -1;
-    cudaError_t e = cudaMemsetAsync(R.sync, 0, (2 + (size_t)R.NB) * sizeof(unsigned), s);
+    // consecutive launches never share an epoch, so a word left by the last
+    // launch never carries a tag this launch waits for
+    R.epoch = 1 + (Rs->epoch++ % 4095u);
+    cudaError_t e = cudaMemsetAsync(R.sync, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return cuda_fail(e, "resident sync reset");
     Dev D = P->dev;
     SolveArgs Ac = A;

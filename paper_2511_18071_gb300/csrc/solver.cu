@@ -124,11 +124,20 @@ static bool mixed(const Problem *P) { return P->params.precision == SW_PRECISION
 int setup_streamed(Problem *P);                                   // streamed.cu
 int solve_streamed(Problem *P, const SolveArgs &A, cudaStream_t s);  // streamed.cu
 int setup_resident(Problem *P);                                   // resident.cu
+bool resident_fits(const Problem *P, int nsm, int *C_out, size_t *smem_out);   // resident.cu
 int solve_resident(Problem *P, const SolveArgs &A, cudaStream_t s);  // resident.cu
 
 int setup_solver_launch(Problem *P) {
     int ex = P->params.executor;
-    if (ex == SW_EXEC_AUTO) ex = P->m >= SW_EXEC_STREAMED_MIN ? SW_EXEC_STREAMED : SW_EXEC_PERSISTENT;
+    if (ex == SW_EXEC_AUTO) {
+        // small periodic 2-D FP64 problems: resident; otherwise by size
+        int nsm = 0, C = 0;
+        size_t rs = 0;
+        cudaError_t e0 = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "SM count");
+        if (resident_fits(P, nsm, &C, &rs)) ex = SW_EXEC_RESIDENT;
+        else ex = P->m >= SW_EXEC_STREAMED_MIN ? SW_EXEC_STREAMED : SW_EXEC_PERSISTENT;
+    }
     P->exec = ex;
     if (ex == SW_EXEC_STREAMED) {
         int rc = setup_streamed(P);
@@ -332,6 +341,7 @@ extern "C" int sw_get_stats(sw_problem *pp, sw_stats *out) {
     out->launches = P->launches;
     out->model_flops = st.model_flops;
     out->model_bytes = st.model_bytes;
+    out->executor = P->exec;
     return SW_OK;
 }
 

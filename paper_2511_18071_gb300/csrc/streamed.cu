@@ -20,6 +20,7 @@
 #include <utility>
 #include <vector>
 
+#include "sw_colapply.cuh"
 #include "sw_solve.cuh"
 
 namespace sw {
@@ -86,6 +87,50 @@ __global__ void __launch_bounds__(NTHREADS) sk_apply_vj(Dev D, Tiling tl, const 
     LdVec<TI, TI> ld{V + (size_t)j * D.m, TI(ss->scale[j])};
     StVec<TI, TI> st{t};
     for (int tile = blockIdx.x; tile < tl.ntiles; tile += gridDim.x) apply_tile<TI, WM>(D, tl, tile, sp, sq, ld, st);
+}
+
+// The same apply in column-marching form (periodic grids with 10, 18 or 34
+// levels; sw_colapply.cuh), one CX x CY tile per block.
+template <typename TI, int P, bool TD>
+__global__ void __launch_bounds__(NTHREADS, (P <= 18 ? 2 : 1))
+    sk_apply_col(Dev D, const TI *V, int j, const SState *ss, TI *t) {
+    if (ss->stop || ss->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LdVec<TI, TI> ld{V + (size_t)j * D.m, TI(ss->scale[j])};
+    StVec<TI, TI> st{t};
+    col_apply_tile<TI, P, TD>(D, blockIdx.x, smem_raw, ld, st);
+}
+
+template <typename TI, int P, bool TD>
+static const void *col_kernel() { return (const void *)sk_apply_col<TI, P, TD>; }
+
+// Kernel, grid and shared memory of the column-marching apply for this
+// problem, or false when it does not serve the grid.
+template <typename TI>
+static bool col_launch_shape(const Dev &D, const void **k, int *grid, size_t *smem) {
+    if (!colapply_ok(D, D.P)) return false;
+    const bool td = D.three_d != 0;
+    *grid = td ? (D.nx / ColShape<true>::CX) * (D.ny / ColShape<true>::CY) : D.nx / ColShape<false>::CX;
+    switch (D.P) {
+    case 10: *k = td ? col_kernel<TI, 10, true>() : col_kernel<TI, 10, false>();
+             *smem = td ? ColGeom<TI, 10, true>::smem() : ColGeom<TI, 10, false>::smem(); break;
+    case 18: *k = td ? col_kernel<TI, 18, true>() : col_kernel<TI, 18, false>();
+             *smem = td ? ColGeom<TI, 18, true>::smem() : ColGeom<TI, 18, false>::smem(); break;
+    default: *k = td ? col_kernel<TI, 34, true>() : col_kernel<TI, 34, false>();
+             *smem = td ? ColGeom<TI, 34, true>::smem() : ColGeom<TI, 34, false>::smem(); break;
+    }
+    return *smem <= 227 * 1024;
+}
+
+template <typename TI>
+static cudaError_t launch_col(const Dev &D, const TI *V, int j, const SState *ss, TI *t, cudaStream_t s) {
+    const void *k = nullptr;
+    int grid = 0;
+    size_t smem = 0;
+    if (!col_launch_shape<TI>(D, &k, &grid, &smem)) return cudaErrorInvalidValue;
+    Dev Dc = D;
+    void *args[] = {&Dc, (void *)&V, &j, (void *)&ss, &t};
+    return cudaLaunchKernel(k, dim3(grid), dim3(NTHREADS), args, smem, s);
 }
 
 // r = b - A x with per-block partial sums of r^2 in part[blockIdx.x]
@@ -688,6 +733,7 @@ __global__ void sk_ctl_final(const double *partA, int nbA, SState *ss, CtlArgs c
 // ---- host side -------------------------------------------------------------
 
 struct Streamed {
+    bool col = false;                            // Arnoldi apply in column-marching form (autotuned)
     cudaGraphExec_t cycle = nullptr;             // the Arnoldi steps of one restart cycle
     long long cycle_kernels = 0;
     SState *ss = nullptr;
@@ -793,6 +839,25 @@ static Tiling tune_tiles(Problem *P) {
         cudaEventElapsedTime(&ms, a, b);
         if (ms < best_ms) { best_ms = ms; best = t; }
     }
+    // the column-marching form competes with the best tile shape
+    {
+        const void *k = nullptr;
+        int grid = 0;
+        size_t smc = 0;
+        if (WM == 0 && col_launch_shape<TI>(D, &k, &grid, &smc) &&
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc) == cudaSuccess) {
+            bool ok = launch_col<TI>(D, V, 0, S->ss, tw, cs) == cudaSuccess;
+            ok = ok && cudaEventRecord(a, cs) == cudaSuccess;
+            for (int r = 0; r < 3 && ok; ++r) ok = launch_col<TI>(D, V, 0, S->ss, tw, cs) == cudaSuccess;
+            ok = ok && cudaEventRecord(b, cs) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess;
+            float ms = 0.f;
+            if (ok && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                S->col = true;
+            }
+        }
+        (void)cudaGetLastError();
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaStreamDestroy(cs);
@@ -877,7 +942,8 @@ static long long enqueue_cycle(const Problem *P, TI *V, TI *tw, SState *ss, doub
     long long n = 0;
     for (int j = 0; j < P->params.restart; ++j) {
         TI *w = V + (size_t)(j + 1) * m;
-        sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, j, ss, tw);
+        if (S->col) launch_col<TI>(D, V, j, ss, tw, s);
+        else sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, j, ss, tw);
         st_ilu<TI, TI, WM>(P, tw, w, ss, 1, s);
         launch_cgs<TI, 1>(V, j, w, m, ss, partB, s);
         sk_ctl_h<1><<<1, NTHREADS, 0, s>>>(partB, SNB, j, ss);
@@ -1045,3 +1111,150 @@ int solve_streamed(Problem *P, const SolveArgs &A, cudaStream_t s) {
 }
 
 }  // namespace sw
+
+// ---- profiling aid: the hot kernels of an Arnoldi step, timed alone --------
+
+namespace sw {
+
+// Time one class of launches: flush L2 (write `flush`), record, launch, record;
+// reps times after one untimed round; returns the mean in microseconds.
+template <class Launch>
+static double time_launches(cudaStream_t s, void *flush, size_t flush_bytes, int reps, Launch launch) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return -1.0;
+    double tot = 0.0;
+    for (int r = 0; r <= reps; ++r) {
+        cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
+        cudaEventRecord(a, s);
+        launch();
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) { tot = -1.0; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (r > 0) tot += ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return tot < 0.0 ? -1.0 : 1e3 * tot / reps;
+}
+
+template <typename TI, int WM>
+static int profile_streamed(Problem *P, int reps, double *us, int n) {
+    Streamed *S = (Streamed *)P->streamed;
+    const Dev &D = P->dev;
+    const long long m = D.m;
+    TI *V = P->params.precision == SW_PRECISION_MIXED ? (TI *)P->d_V32 : (TI *)P->d_V;
+    TI *tw = (TI *)(P->d_work + m);
+    TI *w = V + (size_t)11 * m;
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "profiling stream");
+    // control state of a running cycle: every kernel does its work
+    SState saved, run;
+    e = cudaMemcpy(&saved, S->ss, sizeof(SState), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { cudaStreamDestroy(s); return cuda_fail(e, "profiling state"); }
+    run = saved;
+    run.stop = 0;
+    run.done = 0;
+    for (int i = 0; i <= MAX_RESTART; ++i) run.scale[i] = 1.0;
+    for (int i = 0; i < MAX_RESTART; ++i) { run.hs[i] = 0.0; run.hs32[i] = 0.f; }
+    e = cudaMemcpy(S->ss, &run, sizeof(SState), cudaMemcpyHostToDevice);
+    const size_t fb = (size_t)256 << 20;
+    void *flush = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&flush, fb);
+    if (e != cudaSuccess) { cudaStreamDestroy(s); return cuda_fail(e, "profiling set-up"); }
+    const Tiling &tl = S->tl;
+    const size_t smI = tile_smem<TI>(D, tl);
+    const int ng = D.ngroups;
+    double t[8];
+    t[0] = time_launches(s, flush, fb, reps, [&] {
+        if (S->col) launch_col<TI>(D, V, 0, S->ss, tw, s);
+        else sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, 0, S->ss, tw);
+    });
+    t[1] = time_launches(s, flush, fb, reps, [&] {
+        for (int c = 0; c < ng; ++c) {
+            const long long rows = (long long)(P->goff_h[c + 1] - P->goff_h[c]) * D.P;
+            launch_gather<TI, TI, true, WM>(D, c, (int)((rows + NTHREADS - 1) / NTHREADS), tw, w, S->ss, 0, s);
+        }
+    });
+    t[2] = time_launches(s, flush, fb, reps, [&] {
+        for (int up = 0; up < 2; ++up)
+            for (int c = 0; c < ng; ++c) {
+                const int per = P->goff_h[c + 1] - P->goff_h[c];
+                sk_ilu_product<TI, WM><<<(per * 32 + NTHREADS - 1) / NTHREADS, NTHREADS, 0, s>>>(D, c, w, up, S->ss, 0);
+            }
+    });
+    t[3] = time_launches(s, flush, fb, reps, [&] {
+        for (int c = ng - 2; c >= 0; --c) {
+            const long long rows = (long long)(P->goff_h[c + 1] - P->goff_h[c]) * D.P;
+            launch_gather<TI, TI, false, WM>(D, c, (int)((rows + NTHREADS - 1) / NTHREADS), w, w, S->ss, 0, s);
+        }
+    });
+    t[4] = time_launches(s, flush, fb, reps, [&] { launch_cgs<TI, 1>(V, 10, w, m, S->ss, S->partB, s); });
+    t[5] = time_launches(s, flush, fb, reps, [&] { launch_cgs<TI, 2>(V, 10, w, m, S->ss, S->partB, s); });
+    t[6] = time_launches(s, flush, fb, reps, [&] { launch_cgs<TI, 3>(V, 10, w, m, S->ss, S->partB, s); });
+    t[7] = time_launches(s, flush, fb, reps, [&] { st_ilu<TI, TI, WM>(P, tw, w, S->ss, 0, s); });
+    e = cudaStreamSynchronize(s);
+    cudaFree(flush);
+    cudaError_t e2 = cudaMemcpy(S->ss, &saved, sizeof(SState), cudaMemcpyHostToDevice);
+    cudaStreamDestroy(s);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "profiling");
+    for (int i = 0; i < n && i < 8; ++i) us[i] = t[i];
+    return SW_OK;
+}
+
+}  // namespace sw
+
+using namespace sw;
+
+extern "C" int sw_profile_kernels(sw_problem *pp, int reps, double *us, int n) {
+    Problem *P = (Problem *)pp;
+    if (!P || !us || n < 1 || reps < 1) { set_error("bad argument"); return SW_ERR_BAD_ARG; }
+    if (P->exec != SW_EXEC_STREAMED || !P->streamed) {
+        set_error("kernel profiling needs a problem on the streamed executor");
+        return SW_ERR_BAD_ARG;
+    }
+    if (P->n_solves < 1) { set_error("kernel profiling needs one solve first"); return SW_ERR_BAD_ARG; }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "profiling sync");
+    const bool f32 = P->params.precision == SW_PRECISION_MIXED;
+    if (P->dev.walls) return f32 ? profile_streamed<float, 1>(P, reps, us, n) : profile_streamed<double, 1>(P, reps, us, n);
+    return f32 ? profile_streamed<float, 0>(P, reps, us, n) : profile_streamed<double, 0>(P, reps, us, n);
+}
+
+extern "C" int sw_autotuned_apply(sw_problem *pp, int *column_form, int *tile_x, int *tile_y) {
+    Problem *P = (Problem *)pp;
+    if (!P || !column_form || !tile_x || !tile_y) { set_error("null argument"); return SW_ERR_BAD_ARG; }
+    if (P->exec != SW_EXEC_STREAMED || !P->streamed) { set_error("not on the streamed executor"); return SW_ERR_BAD_ARG; }
+    Streamed *S = (Streamed *)P->streamed;
+    *column_form = S->col ? 1 : 0;
+    *tile_x = S->col ? (P->dev.three_d ? ColShape<true>::CX : ColShape<false>::CX) : S->tl.TX;
+    *tile_y = S->col ? (P->dev.three_d ? ColShape<true>::CY : ColShape<false>::CY) : S->tl.TY;
+    return SW_OK;
+}
+
+extern "C" int sw_set_apply_form(sw_problem *pp, int column_form) {
+    Problem *P = (Problem *)pp;
+    if (!P || (column_form != 0 && column_form != 1)) { set_error("bad argument"); return SW_ERR_BAD_ARG; }
+    if (P->exec != SW_EXEC_STREAMED || !P->streamed) { set_error("not on the streamed executor"); return SW_ERR_BAD_ARG; }
+    Streamed *S = (Streamed *)P->streamed;
+    if (column_form) {
+        const bool f32 = P->params.precision == SW_PRECISION_MIXED;
+        const void *k = nullptr;
+        int grid = 0;
+        size_t smem = 0;
+        const bool ok = !P->dev.walls && (f32 ? col_launch_shape<float>(P->dev, &k, &grid, &smem)
+                                              : col_launch_shape<double>(P->dev, &k, &grid, &smem));
+        if (!ok) { set_error("the column-marching operator does not serve this grid"); return SW_ERR_BAD_ARG; }
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "column apply attribute");
+    }
+    S->col = column_form != 0;
+    if (S->cycle) {   // the restart cycle is captured again at the next solve
+        cudaGraphExecDestroy(S->cycle);
+        S->cycle = nullptr;
+    }
+    return SW_OK;
+}

@@ -1,0 +1,207 @@
+// Column-marching form of the matrix-free operator y = A(eta^(i-1), eta^(i)) p
+// (Eq. 16-18) for periodic grids with a compile-time number of levels P
+// (the streamed executor's large problems).
+//
+// One thread per column of a CX x CY tile.  The tile and its three-column halo
+// are staged in shared memory plane by plane (coalesced rows along x); each
+// thread then computes D_sigma p for its own column and for at most one halo
+// column, with the column's P values in registers (the sigma windows are
+// compile-time: clamp(l - 3, 0, P - 7)), writes it to shared memory, and
+// finally forms the rows of its own column: x and y neighbours from shared
+// memory, the sigma terms and its own D_sigma p from registers, the column's
+// transform coefficients loaded once for all levels.  The arithmetic is that
+// of apply_tile_t (sw_device.cuh), term by term in the same order.
+#pragma once
+#include "sw_device.cuh"
+
+namespace sw {
+
+template <bool TD> struct ColShape;
+template <> struct ColShape<true> { static constexpr int CX = 32, CY = 8; };    // 3-D: 32 x 8 columns
+template <> struct ColShape<false> { static constexpr int CX = 256, CY = 1; };  // 2-D: 256 columns
+
+template <typename T, int P, bool TD>
+struct ColGeom {
+    static constexpr int CX = ColShape<TD>::CX, CY = ColShape<TD>::CY;
+    static constexpr int HX = CX + 2 * HALF, HY = TD ? CY + 2 * HALF : 1;
+    static constexpr int HW = HX * HY;
+    // halo positions a row needs: three rows above and below the tile (interior
+    // x only) and three columns left and right of it (interior y only); the
+    // corners are never read.  At most one per thread.
+    static constexpr int NHALO = TD ? 2 * HALF * CX + 2 * HALF * CY : 2 * HALF;
+    static_assert(NHALO <= CX * CY, "one halo column per thread");
+    static constexpr size_t smem() { return (2 * (size_t)HW * P + 2 * (size_t)P * W) * sizeof(T); }
+};
+
+// whether the column-marching operator serves this grid
+__host__ __device__ inline bool colapply_ok(const Dev &D, int P) {
+    if (D.walls || (P != 10 && P != 18 && P != 34)) return false;
+    if (D.three_d) return D.nx % ColShape<true>::CX == 0 && D.ny % ColShape<true>::CY == 0;
+    return D.nx % ColShape<false>::CX == 0;
+}
+
+template <typename T, int P, bool TD, class Loader, class Store>
+__device__ inline void col_apply_tile(const Dev &D, int tile, unsigned char *smem, Loader &ld, Store &st) {
+    using G = ColGeom<T, P, TD>;
+    constexpr int CX = G::CX, CY = G::CY, HX = G::HX, HW = G::HW;
+    T *sp = reinterpret_cast<T *>(smem);
+    T *sq = sp + (size_t)HW * P;
+    T *sw1 = sq + (size_t)HW * P;
+    T *sw2 = sw1 + P * W;
+    const int tid = threadIdx.x;
+    const int ntx = D.nx / CX;
+    const int tx0 = (tile % ntx) * CX, ty0 = (tile / ntx) * CY;
+    const int n = D.ncol;
+    // sigma weights of every level
+    {
+        const T *w1 = Prec<T>::ws1(D), *w2 = Prec<T>::ws2(D);
+        for (int i = tid; i < P * W; i += CX * CY) {
+            sw1[i] = w1[i];
+            sw2[i] = w2[i];
+        }
+    }
+    // positions of this thread: its own column, then at most one halo column
+    const int txo = tid % CX, tyo = tid / CX;
+    const int own = (tyo + (TD ? HALF : 0)) * HX + txo + HALF;
+    const int gxo = tx0 + txo, gyo = ty0 + tyo;
+    const int gco = gyo * D.nx + gxo;
+    int hpos = -1, hcol = -1;
+    if (tid < G::NHALO) {
+        int a, b;
+        if (TD) {
+            if (tid < 2 * HALF * CX) {          // rows 0..2 and CY+3..CY+5, x inside the tile
+                const int r = tid / CX;
+                a = HALF + tid % CX;
+                b = r < HALF ? r : r + CY;
+            } else {                            // columns 0..2 and CX+3..CX+5, y inside the tile
+                const int mq = tid - 2 * HALF * CX, e = mq % (2 * HALF);
+                b = HALF + mq / (2 * HALF);
+                a = e < HALF ? e : CX + e;
+            }
+        } else {
+            b = 0;
+            a = tid < HALF ? tid : CX + tid;
+        }
+        hpos = b * HX + a;
+        const int gx = wrapi(tx0 + a - HALF, D.nx);
+        const int gy = TD ? wrapi(ty0 + b - HALF, D.ny) : 0;
+        hcol = gy * D.nx + gx;
+    }
+    // stage p
+    T pc[P], ph[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+        pc[l] = ld((long long)l * n + gco);
+        if (hpos >= 0) ph[l] = ld((long long)l * n + hcol);
+    }
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+        sp[l * HW + own] = pc[l];
+        if (hpos >= 0) sp[l * HW + hpos] = ph[l];
+    }
+    __syncthreads();
+    // q = D_sigma p in registers (own column) and in shared memory (both)
+    T qc[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+        constexpr int LAST = P - W;
+        const int s0 = l - HALF < 0 ? 0 : (l - HALF > LAST ? LAST : l - HALF);
+        T a = T(0), b = T(0);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            a += sw1[l * W + k] * pc[s0 + k];
+            if (hpos >= 0) b += sw1[l * W + k] * ph[s0 + k];
+        }
+        qc[l] = a;
+        sq[l * HW + own] = a;
+        if (hpos >= 0) sq[l * HW + hpos] = b;
+    }
+    __syncthreads();
+    // rows of the own column
+    const T *cc = Prec<T>::cc(D);
+    const T ap0 = cc[CC_AP0 * n + gco], ap1 = cc[CC_AP1 * n + gco];
+    const T axp0 = cc[CC_AXP0 * n + gco], axp1 = cc[CC_AXP1 * n + gco];
+    const T bp0 = cc[CC_BP0 * n + gco], bp1 = cc[CC_BP1 * n + gco];
+    const T ef = cc[CC_EF * n + gco];
+    const T gs = cc[CC_GS * n + gco], gxc = cc[CC_GX * n + gco];
+    T gyc = T(0), ay0 = T(0), ay1 = T(0), ayy0 = T(0), ayy1 = T(0), by0 = T(0), by1 = T(0);
+    if (TD) {
+        gyc = cc[CC_GY * n + gco];
+        ay0 = cc[CC_AY0 * n + gco];
+        ay1 = cc[CC_AY1 * n + gco];
+        ayy0 = cc[CC_AYY0 * n + gco];
+        ayy1 = cc[CC_AYY1 * n + gco];
+        by0 = cc[CC_BY0 * n + gco];
+        by1 = cc[CC_BY1 * n + gco];
+    }
+    T wx1[W], wx2[W], wy1[W], wy2[W];
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        wx1[t] = Prec<T>::wx1(D)[t];
+        wx2[t] = Prec<T>::wx2(D)[t];
+        if (TD) {
+            wy1[t] = Prec<T>::wy1(D)[t];
+            wy2[t] = Prec<T>::wy2(D)[t];
+        }
+    }
+    const T inv_nzm1 = T(1) / T(D.nz - 1);
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+        T y;
+        const T *pl = sp + l * HW + own;
+        const T *ql = sq + l * HW + own;
+        if (l == P - 1) {
+            y = pc[l];
+        } else if (l == 0) {
+            const T *p1 = sp + HW + own;
+            T px = T(0), py = T(0);
+#pragma unroll
+            for (int t = -HALF; t <= HALF; ++t) {
+                px += wx1[t + HALF] * (t == 0 ? pc[1] : p1[t]);
+                if (TD) py += wy1[t + HALF] * (t == 0 ? pc[1] : p1[t * HX]);
+            }
+            y = gs * qc[1] + gxc * px;
+            if (TD) y += gyc * py;
+        } else {
+            const T sg = T(l - 1) * inv_nzm1;
+            const T aa = ap0 - sg * ap1;
+            const T bb = bp0 - sg * bp1;
+            const T ax = axp0 - sg * axp1 - aa * ap1;
+            const T c_xs = aa + bb;
+            T c_ss = aa * bb + ef;
+            const T c_s = ax - bb * ap1;
+            T pxx = T(0), pxs = T(0);
+#pragma unroll
+            for (int t = -HALF; t <= HALF; ++t) {
+                pxx += wx2[t + HALF] * (t == 0 ? pc[l] : pl[t]);
+                pxs += wx1[t + HALF] * (t == 0 ? qc[l] : ql[t]);
+            }
+            constexpr int LAST = P - W;
+            const int s0 = l - HALF < 0 ? 0 : (l - HALF > LAST ? LAST : l - HALF);
+            T pss = T(0);
+#pragma unroll
+            for (int k = 0; k < W; ++k) pss += sw2[l * W + k] * pc[s0 + k];
+            y = pxx + c_xs * pxs + c_s * qc[l];
+            if (TD) {
+                const T ay = ay0 - sg * ay1;
+                const T by = by0 - sg * by1;
+                const T ayy = ayy0 - sg * ayy1 - ay * ay1;
+                c_ss += ay * by;
+                const T c_ys = ay + by;
+                const T c_sy = ayy - by * ay1;
+                T pyy = T(0), pys = T(0);
+#pragma unroll
+                for (int t = -HALF; t <= HALF; ++t) {
+                    pyy += wy2[t + HALF] * (t == 0 ? pc[l] : pl[t * HX]);
+                    pys += wy1[t + HALF] * (t == 0 ? qc[l] : ql[t * HX]);
+                }
+                y += pyy + c_ys * pys + c_sy * qc[l];
+            }
+            y += c_ss * pss;
+        }
+        st((long long)l * n + gco, y);
+    }
+    __syncthreads();
+}
+
+}  // namespace sw

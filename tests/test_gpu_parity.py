@@ -363,3 +363,33 @@ def test_resident_wait_bound_reports_timeout(sw):
     assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
     with pytest.raises(sw.SawaveError):
         sw.test_stall_exchange(sw.Problem(nx, 1, nz, L, 0.0, np.ones(nx), executor="persistent").handle, 1)
+
+
+@pytest.mark.parametrize("dims", [(32, 16, 17), (512, 1, 17), (256, 1, 33)], ids=["3d_32x16x17", "2d_512x17", "2d_256x33"])
+@pytest.mark.parametrize("form", [0, 1], ids=["tile", "column"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_streamed_apply_forms(sw, dims, form, precision):
+    # the streamed executor's two operator forms (staged tile, column marching),
+    # forced, on grids the column form serves: a solve to 1e-12 against the oracle
+    nx, ny, nz = dims
+    L = 2 * math.pi
+    X, Y = np.meshgrid(np.arange(nx) * (L / nx), np.arange(ny) * (L / ny), indexing="xy")
+    h = (1.0 + 0.2 * np.exp(-((X - 3) ** 2 + (Y - 2) ** 2))).ravel() if ny > 1 else 1.0 - 0.3 * np.exp(-3 * (X.ravel() - 3.0) ** 2)
+    ly = L if ny > 1 else 0.0
+    kw = dict(restart=20, max_restarts=400, tol=1e-12, guess="cold")
+    gpu = sw.Problem(nx, ny, nz, L, ly, h, executor="streamed", precision=precision, **kw)
+    sw.set_apply_form(gpu.handle, form)
+    assert sw.autotuned_apply(gpu.handle)[0] == form
+    ora = O.OracleProblem(nx, ny, nz, L, ly, h, **kw)
+    e1, e2 = _surfaces(nx, ny, 24)
+    b = _rhs(ora, nz, 25)
+    xo, so, co = ora.solve(e1, e2, b)
+    x = torch.zeros(gpu.m, dtype=torch.float64, device=DEV)
+    gpu.solve(_t(e1), _t(e2), _t(b), x)
+    sg = gpu.stats()
+    assert co == 0 and sg["status"] == 0, (so, sg)
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err <= 1e-10, (err, so, sg)
+    if precision == "fp64":
+        assert abs(sg["iterations"] - so["iterations"]) <= 1, (sg, so)
+    gpu.close()
