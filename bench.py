@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-roofline-large", action="store_true")
     ap.add_argument("--n3d-roof", type=int, default=512, help="roofline_large: nx = ny of the 3-D field")
     ap.add_argument("--members", type=int, default=512, help="batch512: number of instances")
+    ap.add_argument("--batch-budget", type=float, default=240.0, help="batch512: seconds per phase at most")
     ap.add_argument("--clusters", default="1,4,8", help="batch512: thread blocks per member to measure")
     ap.add_argument("--spinup", type=int, default=800, help="flume2048: steps from rest before timing")
     ap.add_argument("--n3d", type=int, default=256, help="bumpy3d: nx = ny (512 for the roofline size)")
@@ -64,7 +65,7 @@ def parse():
     # decay sweep 40 timed steps after 8; the 3-D field 3 after 3; the batch one
     # step after 7 (past the 30 previous-solution solves that fill the history)
     steps, warm = {"stokes512": (40, 8), "decay_sweep": (40, 8), "flume2048": (40, 8), "bumpy3d": (3, 3),
-                   "batch512": (1, 7), "sf_sweep": (200, 6)}[a.workload]
+                   "batch512": (2, 0), "sf_sweep": (200, 6)}[a.workload]
     if a.steps is None:
         a.steps = steps
     if a.warmup is None:
@@ -680,10 +681,15 @@ def bumpy3d_arm(args):
 
 
 def batch512_arm(args):
-    """512 uneven 2-D instances: one batched launch per step vs the same instances one by one."""
+    """Config 5: 512 uneven 2-D instances advanced in one batched launch per
+    stage, against the same instances advanced one by one through the
+    single-problem API.  From rest at t = 0: the history fill (N_INIT_STEPS
+    steps on the previous-solution guess, batched, timed), then K EWMA steps
+    batched (timed), then K further EWMA steps of the same instances one by one
+    (timed; every instance continues its own trajectory and history).  Progress
+    goes to stderr; a phase stops early at --batch-budget seconds and says so."""
     import concurrent.futures as cf
 
-    import numpy as np
     import torch
 
     import __graft_entry__ as ge
@@ -693,62 +699,73 @@ def batch512_arm(args):
     dev = torch.device("cuda", 0)
     members = W.batch_members(n=args.members)
     prec = "mixed"
-    t0 = time.perf_counter()
+    log = lambda *a: print("[batch512 %.1fs]" % (time.perf_counter() - T0), *a, file=sys.stderr, flush=True)
+    T0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=16) as ex:
         probs = list(ex.map(lambda wl: sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], precision=prec,
                                                    **solver_kw(args, "ewma")), members))
-    create_s = time.perf_counter() - t0
     for P, wl in zip(probs, members):
         sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
         sw.set_state(P.handle, _t(torch, dev, wl["u"]), None, _t(torch, dev, wl["w"]), _t(torch, dev, wl["eta"]))
-    B = sw.Batch(probs)
-    for _ in range(args.warmup * 5):
-        B.advance_stage()
     torch.cuda.synchronize()
-    variants = {}
-    with ClockSampler(0) as clk:
-        for cs in [int(c) for c in args.clusters.split(",")]:
-            try:
-                B.set_cluster(cs)
-            except sw.SawaveError as err:
-                variants[str(cs)] = {"unavailable": str(err)}
-                continue
-            it0 = sum(sw.get_stats(P.handle)["total_iterations"] for P in probs)
+    create_s = time.perf_counter() - T0
+    log("created %d problems" % len(probs))
+    B = sw.Batch(probs)
+    cs = [int(c) for c in args.clusters.split(",")][0]
+    B.set_cluster(cs)
+
+    def phase(name, nsteps, one_stage):
+        it0 = sum(sw.get_stats(P.handle)["total_iterations"] for P in probs)
+        t0 = time.perf_counter()
+        ms, done = 0.0, 0
+        for step in range(nsteps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            for _ in range(args.steps * 5):
-                B.advance_stage()
+            for _ in range(5):
+                one_stage()
             b.record()
             torch.cuda.synchronize()
-            ms_v = a.elapsed_time(b)
-            it1 = sum(sw.get_stats(P.handle)["total_iterations"] for P in probs)
-            nsolve = len(probs) * 5 * args.steps
-            variants[str(cs)] = {"value": nsolve / (ms_v / 1e3), "ms_per_step": ms_v / args.steps,
-                                 "iters_per_solve": (it1 - it0) / nsolve}
-    best = max((k for k in variants if "value" in variants[k]), key=lambda k: variants[k]["value"])
-    batched = variants[best]["value"]
-    ms = variants[best]["ms_per_step"] * args.steps
-    nsolve = len(probs) * 5 * args.steps
-    # the same instances advanced one by one (one step) with the single-problem API
-    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a2.record()
-    for P in probs:
-        for _ in range(5):
+            ms += a.elapsed_time(b)
+            done += 1
+            log("%s step %d: %.1f ms" % (name, step + 1, a.elapsed_time(b)))
+            if time.perf_counter() - t0 > args.batch_budget:
+                break
+        it1 = sum(sw.get_stats(P.handle)["total_iterations"] for P in probs)
+        n = len(probs) * 5 * done
+        stats = [sw.get_stats(P.handle) for P in probs]
+        bad = [{"member": members[i]["name"], "status": s["status"], "iterations": s["iterations"]}
+               for i, s in enumerate(stats) if s["status"] != 0]
+        worst = max(range(len(probs)), key=lambda i: stats[i]["iterations"])
+        return {"value": n / (ms / 1e3), "ms": ms, "steps": done, "steps_asked": nsteps, "solves": n,
+                "iters_per_solve": (it1 - it0) / n, "members_not_ok": len(bad), "not_ok": bad[:4],
+                "last_stage_max_iters": {"member": members[worst]["name"],
+                                         "iterations": stats[worst]["iterations"]}}
+
+    def one_by_one():
+        for P in probs:
             sw.advance_stage(P.handle)
-    b2.record()
-    torch.cuda.synchronize()
-    ms1 = a2.elapsed_time(b2)
-    single = len(probs) * 5 / (ms1 / 1e3)
-    line = {"metric": METRIC, "value": batched, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "iters_per_solve": variants[best]["iters_per_solve"], "blocks_per_member": int(best),
-            "by_blocks_per_member": variants,
-            "one_by_one": {"value": single, "steps": 1}, "speedup_vs_one_by_one": batched / single,
-            "create_s": create_s, "clocks": clk.summary(), "gpu_launches_per_step": 5 * 7,
-            "config": {"workload": "batch512_uneven_2d", "instances": len(probs),
+
+    with ClockSampler(0) as clk:
+        fill = phase("fill (batched)", N_INIT_STEPS, B.advance_stage)
+        ewma_b = phase("ewma (batched)", args.steps, B.advance_stage)
+        ewma_s = phase("ewma (one by one)", args.steps, one_by_one)
+    B.close()
+    for P in probs:
+        P.close()
+    line = {"metric": METRIC, "value": ewma_b["value"], "unit": UNIT, "n_gpus": 1, "steps": ewma_b["steps"],
+            "warmup": N_INIT_STEPS, "ms_per_step": ewma_b["ms"] / max(ewma_b["steps"], 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "value_is": "batched solves/s over the EWMA steps after the history fill",
+            "iters_per_solve": ewma_b["iters_per_solve"], "blocks_per_member": cs,
+            "fill_batched": fill, "ewma_batched": ewma_b, "ewma_one_by_one": ewma_s,
+            "speedup_vs_one_by_one": ewma_b["value"] / ewma_s["value"],
+            "create_s": create_s, "clocks": clk.summary(), "gpu_launches_per_stage_batched": 7,
+            "config": {"workload": "batch512_uneven_2d", "instances": len(members),
                        "unknowns_total": int(sum(wl["m"] for wl in members)), "guess": "ewma", "k": args.k,
-                       "decay": args.decay, "tol": 1e-8, "restart": 20, "precision": prec}}
+                       "decay": args.decay, "tol": 1e-8, "restart": 20, "precision": prec,
+                       "history_fill_steps": N_INIT_STEPS,
+                       "one_by_one": "the same instances, continuing their trajectories, through sw_advance_stage "
+                                     "(each on the executor chosen for it)"}}
     print(json.dumps(line), flush=True)
 
 
@@ -855,7 +872,8 @@ def sf_sweep_arm(args):
     """Stream-function waves over the kh x steepness grid of the paper's study
     (200 x 20 periodic slice, dt = 1e-4 s, six untimed steps on the previous
     solution, then the timed steps): previous solution vs the range finder
-    (K = 15, k = 10, V = X Omega) vs EWMA (k = 10, r = 0.7)."""
+    (K = 15, k = 10, V = X Omega) vs EWMA (k = 10, r = 0.7), and both subspace
+    guesses again with V = Q (rrf_q, ewma_q: the orthonormalised sketch)."""
     import torch
 
     import __graft_entry__ as ge
@@ -873,10 +891,12 @@ def sf_sweep_arm(args):
                 wl = W.stream_function_2d(kh=kh, steepness=steep, dt=1e-4)
                 row = {"kh": kh, "steepness_of_max": steep, "H_over_L": wl["height"] / wl["lx"],
                        "fourier_modes": wl["wave"].N}
-                for guess in ("previous", "rrf", "ewma"):
-                    kw = solver_kw(a, guess)
-                    if guess == "rrf":
+                for guess in ("previous", "rrf", "ewma", "rrf_q", "ewma_q"):
+                    kw = solver_kw(a, guess.replace("_q", ""))
+                    if guess.startswith("rrf"):
                         kw["history"] = 15
+                    if guess.endswith("_q"):
+                        kw["orthonormalize"] = True   # V = Q, the optional QR step of Algorithms 3 and 4
                     P = sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], precision="fp64", **kw)
                     sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
                     sw.set_state(P.handle, _t(torch, dev, wl["u"]), None, _t(torch, dev, wl["w"]),
@@ -890,7 +910,7 @@ def sf_sweep_arm(args):
                     if guess == "ewma":
                         tot_solves += 5 * args.steps
                         tot_ms += r["ms_per_step"] * args.steps
-                for guess in ("rrf", "ewma"):
+                for guess in ("rrf", "ewma", "rrf_q", "ewma_q"):
                     row[guess]["iter_speedup"] = row["previous"]["iters_per_step"] / row[guess]["iters_per_step"] \
                         if row[guess]["iters_per_step"] else None
                     row[guess]["time_speedup"] = row["previous"]["ms_per_step"] / row[guess]["ms_per_step"]

@@ -135,7 +135,7 @@ static const void *block_kern(bool mixed) { return mixed ? batch_kernel_block_f3
 // can hold at once (0 when it cannot place one).
 static int cluster_capacity(Batch *B, int cs) {
     const void *kern = cluster_kern(B->mixed);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem);
+    cudaError_t e = ensure_smem((const void *)kern, (size_t)(int)B->smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) { (void)cudaGetLastError(); return 0; }
     cudaLaunchConfig_t cfg = {};
@@ -213,7 +213,7 @@ extern "C" int sw_create_batch(sw_problem *const *problems, int n, sw_batch **ou
     }
     B->smem = BSMEM_FIXED + tiles;
     const void *kern = block_kern(B->mixed);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem);
+    cudaError_t e = ensure_smem((const void *)kern, (size_t)(int)B->smem);
     int nsm = 0, per = 0, dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

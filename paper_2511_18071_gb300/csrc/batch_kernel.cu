@@ -32,7 +32,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_solve_kernel(const BatchIte
         const Dev D = items[i].D;
         const SolveArgs A = items[i].A;
         BlockTeam tm;
-        solve_body<BlockTeam, TI, BATCH_WM>(tm, D, A, S, smem_raw + BSMEM_FIXED, nullptr);
+        double ph[PH_COUNT];   // per-phase device time of this member's solve (thread 0)
+        for (int q = 0; q < PH_COUNT; ++q) ph[q] = 0.0;
+        solve_body<BlockTeam, TI, BATCH_WM>(tm, D, A, S, smem_raw + BSMEM_FIXED, ph);
         __syncthreads();
     }
 }
@@ -55,7 +57,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) batch_solve_cluster_kernel(const 
         const Dev D = items[i].D;
         const SolveArgs A = items[i].A;
         ClusterTeam tm(S.xchg);
-        solve_body<ClusterTeam, TI, BATCH_WM>(tm, D, A, S, smem_raw + BSMEM_FIXED, nullptr);
+        double ph[PH_COUNT];
+        for (int q = 0; q < PH_COUNT; ++q) ph[q] = 0.0;
+        solve_body<ClusterTeam, TI, BATCH_WM>(tm, D, A, S, smem_raw + BSMEM_FIXED, ph);
         cl.sync();
     }
 }

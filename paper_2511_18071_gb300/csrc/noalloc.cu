@@ -144,7 +144,7 @@ int na_setup(double **out) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-        e = cudaFuncSetAttribute(na_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        e = ensure_smem((const void *)na_apply_kernel, (size_t)200 * 1024);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         g_dev_ptr[dev] = (double *)p;
     }

@@ -1151,7 +1151,7 @@ int setup_resident(Problem *P) {
     if (e != cudaSuccess) return cuda_fail(e, "resident constants");
     Rs->kern = resident_kernel_for(D.layout);
     Rs->smem = smem;
-    e = cudaFuncSetAttribute(Rs->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem((const void *)Rs->kern, (size_t)(int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "resident smem attribute");
     int per = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, Rs->kern, NTHREADS, smem);

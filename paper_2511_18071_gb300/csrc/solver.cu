@@ -150,10 +150,9 @@ int setup_solver_launch(Problem *P) {
     Tiling t = make_tiling(P->dev);
     size_t smem = solve_smem(P->dev, t);
     const void *kern = solve_kernel_for(P);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem((const void *)kern, (size_t)(int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "solve_kernel smem attribute");
-    e = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * (size_t)P->dev.P * t.HW * sizeof(double)));
+    e = ensure_smem((const void *)apply_kernel, (size_t)(int)(2 * (size_t)P->dev.P * t.HW * sizeof(double)));
     if (e != cudaSuccess) return cuda_fail(e, "apply_kernel smem attribute");
     int nsm = 0, per = 0;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);

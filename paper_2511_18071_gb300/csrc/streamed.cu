@@ -775,14 +775,11 @@ static size_t tile_smem(const Dev &D, const Tiling &t) { return 2 * (size_t)D.P 
 
 template <typename TI, int WM>
 static cudaError_t set_smem_attrs(const Dev &D, const Tiling &t) {
-    cudaError_t e = cudaFuncSetAttribute(sk_apply_vj<TI, WM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tile_smem<TI>(D, t));
+    cudaError_t e = ensure_smem((const void *)sk_apply_vj<TI, WM>, (size_t)(int)tile_smem<TI>(D, t));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sk_apply_resid<WM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tile_smem<double>(D, t));
+        e = ensure_smem((const void *)sk_apply_resid<WM>, (size_t)(int)tile_smem<double>(D, t));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sk_apply_w<WM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tile_smem<double>(D, t));
+        e = ensure_smem((const void *)sk_apply_w<WM>, (size_t)(int)tile_smem<double>(D, t));
     return e;
 }
 
@@ -828,7 +825,7 @@ static Tiling tune_tiles(Problem *P) {
         Tiling t = tiling_with(D, c.first, c.second);
         const size_t sm = tile_smem<TI>(D, t);
         if (sm > 200 * 1024 || t.ntiles < 152) continue;
-        if (cudaFuncSetAttribute(sk_apply_vj<TI, WM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        if (ensure_smem((const void *)sk_apply_vj<TI, WM>, (size_t)(int)sm) !=
             cudaSuccess) { (void)cudaGetLastError(); continue; }
         sk_apply_vj<TI, WM><<<t.ntiles, NTHREADS, sm, cs>>>(D, t, V, 0, S->ss, tw);
         cudaEventRecord(a, cs);
@@ -845,7 +842,7 @@ static Tiling tune_tiles(Problem *P) {
         int grid = 0;
         size_t smc = 0;
         if (WM == 0 && col_launch_shape<TI>(D, &k, &grid, &smc) &&
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc) == cudaSuccess) {
+            ensure_smem((const void *)k, (size_t)(int)smc) == cudaSuccess) {
             bool ok = launch_col<TI>(D, V, 0, S->ss, tw, cs) == cudaSuccess;
             ok = ok && cudaEventRecord(a, cs) == cudaSuccess;
             for (int r = 0; r < 3 && ok; ++r) ok = launch_col<TI>(D, V, 0, S->ss, tw, cs) == cudaSuccess;
@@ -1248,7 +1245,7 @@ extern "C" int sw_set_apply_form(sw_problem *pp, int column_form) {
         const bool ok = !P->dev.walls && (f32 ? col_launch_shape<float>(P->dev, &k, &grid, &smem)
                                               : col_launch_shape<double>(P->dev, &k, &grid, &smem));
         if (!ok) { set_error("the column-marching operator does not serve this grid"); return SW_ERR_BAD_ARG; }
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = ensure_smem((const void *)k, (size_t)(int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "column apply attribute");
     }
     S->col = column_form != 0;

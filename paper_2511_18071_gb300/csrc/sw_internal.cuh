@@ -174,6 +174,12 @@ int sigma_window(int nz, int j);
 void grid_weights(const sw_grid &g, double *wx1, double *wx2, double *wy1, double *wy2, double *ws1, double *ws2,
                   int *win);
 
+// Raise the dynamic shared-memory limit of kernel `kern` to at least `bytes`.
+// The limit is one setting per kernel function shared by every problem, so it
+// only ever grows (a problem created later with a smaller need must not lower
+// it under an earlier one's); thread-safe.
+cudaError_t ensure_smem(const void *kern, size_t bytes);
+
 void set_error(const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 

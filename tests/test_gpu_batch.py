@@ -1,8 +1,10 @@
 """Batch form: many independent problems of uneven size solved in one launch,
-one thread block per problem, against the oracle problem by problem.
-Solves run to 1e-12 agree with the oracle to 1e-10 (FP64 and the FP64-refined
-precision form); the batched stage driver tracks the oracle's stages to 1e-9;
-EWMA iteration counts at 1e-8 match the single-problem path to +-1."""
+one thread block (or cluster) per problem, against the oracle problem by
+problem.  Solves run to 1e-12 agree with the oracle to 1e-10 (FP64 and the
+FP64-refined precision form); the batched stage driver tracks the oracle's
+stages to 1e-9; EWMA iteration counts at 1e-8 match the single-problem path
+to +-1; the 512-member configuration converges in one launch and meets the
+oracle's stopping test on one member of every size class."""
 import math
 
 import numpy as np
@@ -125,3 +127,58 @@ def test_batch_ewma_iterations_match_single(sw, cluster):
             sa, sb = a.stats(), b.stats()
             assert sa["status"] == 0 and sb["status"] == 0
             assert abs(sa["iterations"] - sb["iterations"]) <= 1, (sa, sb)
+
+
+def test_batch512_one_launch_sampled_parity(sw):
+    # The batch form's configuration: 512 uneven members (nx 128..2048, nz 9, 17
+    # or 33, half over a bar), the precision form at tol 1e-8, every member's
+    # first stage (a cold solve: the previous solution is zero) in one batched
+    # stage launch.  Every member must converge; one member of each (nx, nz,
+    # bed) class is checked against the oracle at full size:
+    # - the system: eta^(i-1) is the initial surface bit for bit, and b is the
+    #   oracle's right-hand side (Eq. 20) for the GPU's eta pair within 1e-10
+    #   of max |b|;
+    # - the solution meets the stopping test as the oracle evaluates it,
+    #   ||M^-1 (b - A x)|| <= 1.5 tol ||M^-1 b|| with its own operator and
+    #   factors (x 1.5: the precision form's restart residual goes through the
+    #   FP32 factors), a size-independent check.
+    import concurrent.futures as cf
+    members = W.batch_members(n=512)
+    tol = 1e-8
+    kw = dict(restart=20, max_restarts=1000, tol=tol, guess="previous", precision="mixed")
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        probs = list(ex.map(lambda wl: sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], **kw), members))
+    for p, wl in zip(probs, members):
+        sw.set_physics(p.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+        sw.set_state(p.handle, _t(wl["u"]), None, _t(wl["w"]), _t(wl["eta"]))
+    batch = sw.Batch(probs)
+    batch.advance_stage()
+    torch.cuda.synchronize()
+    bad = [(i, members[i]["name"], p.stats()) for i, p in enumerate(probs) if p.stats()["status"] != 0]
+    assert not bad, bad[:4]
+    classes = {}
+    for i, wl in enumerate(members):
+        classes.setdefault((wl["nx"], wl["nz"], i % 2), i)
+    assert len(classes) == 30
+    for (nx, nz, bar), i in sorted(classes.items()):
+        wl, p = members[i], probs[i]
+        ep = torch.empty(p.ncol, dtype=torch.float64, device=DEV)
+        ec = torch.empty_like(ep)
+        b = torch.empty(p.m, dtype=torch.float64, device=DEV)
+        x = torch.empty_like(b)
+        sw.get_last_system(p.handle, ep, ec, b)
+        sw.get_state(p.handle, pres=x)
+        torch.cuda.synchronize()
+        ep, ec, b, x = (a.cpu().numpy() for a in (ep, ec, b, x))
+        assert np.array_equal(ep, wl["eta"]), wl["name"]
+        ora = O.OracleProblem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], tol=tol)
+        zero = np.zeros(p.m)
+        feta = ora.f_eta(wl["u"], None, wl["w"], wl["eta"])
+        bo = ora.rhs((wl["g"], wl["rho"], wl["dt"]), 1, wl["u"], None, wl["w"], zero, None, zero, ep, ec, feta)
+        assert np.abs(b - bo).max() <= 1e-10 * np.abs(bo).max(), wl["name"]
+        ora.assemble(ep, ec)
+        rel = np.linalg.norm(ora.ilu_apply(b - ora.matvec(x))) / np.linalg.norm(ora.ilu_apply(b))
+        assert rel <= 1.5 * tol, (wl["name"], rel, p.stats())
+    batch.close()
+    for p in probs:
+        p.close()

@@ -82,10 +82,11 @@ def _wl(nx, ny, nz, lx, ly, h, comps, steps, name, **extra):
     return d
 
 
-def airy_2d(nx=64, nz=9, kh=1.0, a_over_h=0.01, depth=1.0, steps=50):
-    """Linear Airy wave in a periodic 2-D slice, flat bed (the 64 x 9 workload)."""
+def airy_2d(nx=64, nz=9, kh=1.0, a_over_h=0.01, depth=1.0, steps=50, waves=1):
+    """Linear Airy wave in a periodic 2-D slice of `waves` wavelengths, flat bed
+    (the 64 x 9 workload: one wavelength)."""
     k = kh / depth
-    lx = 2 * math.pi / k
+    lx = waves * 2 * math.pi / k
     h = np.full(nx, depth)
     return _wl(nx, 1, nz, lx, 0.0, h, [(k, 0.0, a_over_h * depth, 0.0)], steps, "airy2d_%dx%d" % (nx, nz))
 
@@ -113,15 +114,22 @@ def stokes_like_2d(nx=512, nz=17, kh=2.0, a1_over_h=0.08, depth=1.0, n_harm=4, r
 
 
 def periodic_bar_2d(nx=256, nz=9, kh=1.5, a_over_h=0.02, depth=1.0, bar_frac=0.25, bar_height=0.5, seed=7,
-                    steps=50):
-    """Periodic 2-D slice over a trapezoidal bar (variable depth, box pattern)."""
+                    steps=50, max_slope=None, waves=1):
+    """Periodic 2-D slice of `waves` wavelengths over a trapezoidal bar
+    (variable depth, box pattern).
+
+    max_slope: if given, the ramps are widened (up to what keeps the bar off the
+    domain's ends) and then the crest lowered until no ramp is steeper than it."""
     rng = np.random.default_rng(seed)
     k = kh / depth
-    lx = 2 * math.pi / k
+    lx = waves * 2 * math.pi / k
     x = np.arange(nx) * (lx / nx)
     c0 = rng.uniform(0.3, 0.7) * lx
     top = bar_frac * lx * 0.3
     ramp = bar_frac * lx * 0.35
+    if max_slope is not None:
+        ramp = min(max(ramp, bar_height * depth / max_slope), 0.3 * lx - top)
+        bar_height = min(bar_height, max_slope * ramp / depth)
     dist = np.abs(x - c0)
     prof = np.clip((top + ramp - dist) / ramp, 0.0, 1.0)
     h = depth * (1.0 - bar_height * prof)
@@ -167,9 +175,15 @@ def state_arrays(wl):
     return st
 
 
-def batch_members(n=512, seed=5, nxs=(128, 256, 512, 1024, 2048), nzs=(9, 17, 33)):
+def batch_members(n=512, seed=5, nxs=(128, 256, 512, 1024, 2048), nzs=(9, 17, 33), max_slope=0.5, ppw=128):
     """Uneven 2-D members: nx, nz drawn uniformly, kh ~ U[0.5, 3], a/h ~ U[0.005, 0.08],
-    half flat-bottomed, half over a seeded periodic trapezoidal bar."""
+    half flat-bottomed, half over a seeded periodic trapezoidal bar whose ramps
+    are no steeper than max_slope.  Every member resolves its wave with ppw
+    points per wavelength, so a member of nx columns spans nx / ppw
+    wavelengths (uneven sizes are uneven domain lengths at one resolution).
+    On one-wavelength domains of 2,048 columns the x spacing is far below the
+    sigma spacing, and ramps of slope 2 appear on the shortest domains; in both
+    cases restarted GMRES(20) with ILU(0) stagnates."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
@@ -177,10 +191,12 @@ def batch_members(n=512, seed=5, nxs=(128, 256, 512, 1024, 2048), nzs=(9, 17, 33
         nz = int(rng.choice(nzs))
         kh = float(rng.uniform(0.5, 3.0))
         a = float(rng.uniform(0.005, 0.08))
+        waves = max(1, nx // ppw)
         if i % 2 == 0:
-            wl = airy_2d(nx=nx, nz=nz, kh=kh, a_over_h=a, steps=1)
+            wl = airy_2d(nx=nx, nz=nz, kh=kh, a_over_h=a, steps=1, waves=waves)
         else:
-            wl = periodic_bar_2d(nx=nx, nz=nz, kh=kh, a_over_h=a, seed=int(rng.integers(1 << 30)), steps=1)
+            wl = periodic_bar_2d(nx=nx, nz=nz, kh=kh, a_over_h=a, seed=int(rng.integers(1 << 30)), steps=1,
+                                 max_slope=max_slope, waves=waves)
         wl["name"] = "member%03d_%s" % (i, wl["name"])
         out.append(wl)
     return out
