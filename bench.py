@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--n3d-roof", type=int, default=512, help="roofline_large: nx = ny of the 3-D field")
     ap.add_argument("--members", type=int, default=512, help="batch512: number of instances")
     ap.add_argument("--batch-budget", type=float, default=240.0, help="batch512: seconds per phase at most")
-    ap.add_argument("--clusters", default="1,4,8", help="batch512: thread blocks per member to measure")
+    ap.add_argument("--clusters", default="auto",
+                    help="batch512: thread blocks per member (1, 2, 4, 8, 16), or auto for the library's default "
+                         "launch (the largest members on clusters beside single blocks)")
     ap.add_argument("--spinup", type=int, default=800, help="flume2048: steps from rest before timing")
     ap.add_argument("--n3d", type=int, default=256, help="bumpy3d: nx = ny (512 for the roofline size)")
     ap.add_argument("--executor", default="auto", choices=["auto", "persistent", "streamed"],
@@ -70,8 +72,6 @@ def parse():
         a.steps = steps
     if a.warmup is None:
         a.warmup = warm
-    if a.workload == "batch512" and a.clusters == "1,4,8":
-        a.clusters = "16"
     return a
 
 
@@ -683,11 +683,11 @@ def bumpy3d_arm(args):
 def batch512_arm(args):
     """Config 5: 512 uneven 2-D instances advanced in one batched launch per
     stage, against the same instances advanced one by one through the
-    single-problem API.  From rest at t = 0: the history fill (N_INIT_STEPS
-    steps on the previous-solution guess, batched, timed), then K EWMA steps
-    batched (timed), then K further EWMA steps of the same instances one by one
-    (timed; every instance continues its own trajectory and history).  Progress
-    goes to stderr; a phase stops early at --batch-budget seconds and says so."""
+    single-problem API.  Two copies of the instances start from rest at t = 0
+    (the same states, so the same trajectories): the history fill (N_INIT_STEPS
+    steps on the previous-solution guess) and then K EWMA steps, each phase
+    timed batched on one copy and one by one on the other.  Progress goes to
+    stderr; a phase stops early at --batch-budget seconds and says so."""
     import concurrent.futures as cf
 
     import torch
@@ -701,21 +701,31 @@ def batch512_arm(args):
     prec = "mixed"
     log = lambda *a: print("[batch512 %.1fs]" % (time.perf_counter() - T0), *a, file=sys.stderr, flush=True)
     T0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(max_workers=16) as ex:
-        probs = list(ex.map(lambda wl: sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], precision=prec,
-                                                   **solver_kw(args, "ewma")), members))
-    for P, wl in zip(probs, members):
-        sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
-        sw.set_state(P.handle, _t(torch, dev, wl["u"]), None, _t(torch, dev, wl["w"]), _t(torch, dev, wl["eta"]))
+
+    def make():
+        with cf.ThreadPoolExecutor(max_workers=16) as ex:
+            ps = list(ex.map(lambda wl: sw.Problem(wl["nx"], 1, wl["nz"], wl["lx"], 0.0, wl["h"], precision=prec,
+                                                    **solver_kw(args, "ewma")), members))
+        for P, wl in zip(ps, members):
+            sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
+            sw.set_state(P.handle, _t(torch, dev, wl["u"]), None, _t(torch, dev, wl["w"]),
+                         _t(torch, dev, wl["eta"]))
+        return ps
+
+    probs = make()
+    single = make()
     torch.cuda.synchronize()
     create_s = time.perf_counter() - T0
-    log("created %d problems" % len(probs))
+    log("created 2 x %d problems" % len(probs))
     B = sw.Batch(probs)
-    cs = [int(c) for c in args.clusters.split(",")][0]
-    B.set_cluster(cs)
+    if args.clusters != "auto":
+        B.set_cluster(int(args.clusters))
+    shape = B.launch_shape()
+    tile, tile_us = B.autotuned_tile()
+    log("launch shape", shape, "tile", tile, tile_us)
 
-    def phase(name, nsteps, one_stage):
-        it0 = sum(sw.get_stats(P.handle)["total_iterations"] for P in probs)
+    def phase(name, ps, nsteps, one_stage):
+        it0 = sum(sw.get_stats(P.handle)["total_iterations"] for P in ps)
         t0 = time.perf_counter()
         ms, done = 0.0, 0
         for step in range(nsteps):
@@ -729,43 +739,49 @@ def batch512_arm(args):
             done += 1
             log("%s step %d: %.1f ms" % (name, step + 1, a.elapsed_time(b)))
             if time.perf_counter() - t0 > args.batch_budget:
+                log("%s: budget reached after %d of %d steps" % (name, done, nsteps))
                 break
-        it1 = sum(sw.get_stats(P.handle)["total_iterations"] for P in probs)
-        n = len(probs) * 5 * done
-        stats = [sw.get_stats(P.handle) for P in probs]
+        stats = [sw.get_stats(P.handle) for P in ps]
+        it1 = sum(s["total_iterations"] for s in stats)
+        n = len(ps) * 5 * done
         bad = [{"member": members[i]["name"], "status": s["status"], "iterations": s["iterations"]}
                for i, s in enumerate(stats) if s["status"] != 0]
-        worst = max(range(len(probs)), key=lambda i: stats[i]["iterations"])
+        worst = max(range(len(ps)), key=lambda i: stats[i]["iterations"])
         return {"value": n / (ms / 1e3), "ms": ms, "steps": done, "steps_asked": nsteps, "solves": n,
                 "iters_per_solve": (it1 - it0) / n, "members_not_ok": len(bad), "not_ok": bad[:4],
                 "last_stage_max_iters": {"member": members[worst]["name"],
                                          "iterations": stats[worst]["iterations"]}}
 
     def one_by_one():
-        for P in probs:
+        for P in single:
             sw.advance_stage(P.handle)
 
     with ClockSampler(0) as clk:
-        fill = phase("fill (batched)", N_INIT_STEPS, B.advance_stage)
-        ewma_b = phase("ewma (batched)", args.steps, B.advance_stage)
-        ewma_s = phase("ewma (one by one)", args.steps, one_by_one)
+        fill_b = phase("fill (batched)", probs, N_INIT_STEPS, B.advance_stage)
+        fill_s = phase("fill (one by one)", single, N_INIT_STEPS, one_by_one)
+        ewma_b = phase("ewma (batched)", probs, args.steps, B.advance_stage)
+        ewma_s = phase("ewma (one by one)", single, args.steps, one_by_one)
     B.close()
-    for P in probs:
+    for P in probs + single:
         P.close()
     line = {"metric": METRIC, "value": ewma_b["value"], "unit": UNIT, "n_gpus": 1, "steps": ewma_b["steps"],
             "warmup": N_INIT_STEPS, "ms_per_step": ewma_b["ms"] / max(ewma_b["steps"], 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "value_is": "batched solves/s over the EWMA steps after the history fill",
-            "iters_per_solve": ewma_b["iters_per_solve"], "blocks_per_member": cs,
-            "fill_batched": fill, "ewma_batched": ewma_b, "ewma_one_by_one": ewma_s,
+            "iters_per_solve": ewma_b["iters_per_solve"],
+            "fill_batched": fill_b, "fill_one_by_one": fill_s, "ewma_batched": ewma_b, "ewma_one_by_one": ewma_s,
             "speedup_vs_one_by_one": ewma_b["value"] / ewma_s["value"],
+            "speedup_vs_one_by_one_fill": fill_b["value"] / fill_s["value"],
+            "launch": {"members_on_clusters": shape[0], "blocks_per_cluster_member": shape[1],
+                       "cluster_launch_blocks": shape[2], "single_block_launch_blocks": shape[3],
+                       "tile_columns": tile, "tile_us_per_batched_apply": tile_us},
             "create_s": create_s, "clocks": clk.summary(), "gpu_launches_per_stage_batched": 7,
             "config": {"workload": "batch512_uneven_2d", "instances": len(members),
                        "unknowns_total": int(sum(wl["m"] for wl in members)), "guess": "ewma", "k": args.k,
                        "decay": args.decay, "tol": 1e-8, "restart": 20, "precision": prec,
-                       "history_fill_steps": N_INIT_STEPS,
-                       "one_by_one": "the same instances, continuing their trajectories, through sw_advance_stage "
-                                     "(each on the executor chosen for it)"}}
+                       "history_fill_steps": N_INIT_STEPS, "points_per_wavelength": 128,
+                       "one_by_one": "a second copy of the same instances from the same states, through "
+                                     "sw_advance_stage (each on the executor chosen for it)"}}
     print(json.dumps(line), flush=True)
 
 

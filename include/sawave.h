@@ -258,16 +258,41 @@ int sw_destroy_batch(sw_batch *b);
  * problems were given to sw_create_batch.  Per-member results via sw_get_stats. */
 int sw_batch_solve(sw_batch *b, const double *const *d_eta_prev, const double *const *d_eta_cur,
                    const double *const *d_b, double *const *d_x, void *stream);
-/* Thread blocks per member for the batch's solves: 1 gives every member one
- * thread block, so that up to one member per SM run at once; 2, 4,
- * 8 or 16 give every member a thread-block cluster of that many blocks (one
- * per SM, cluster barriers and partial sums through distributed shared
- * memory), which shortens large members at the cost of fewer members at once.
- * The default set by sw_create_batch is a 16-block cluster (or the largest
- * the device can place) when the members average 4,096 unknowns or more, else
- * one block.  SW_ERR_BAD_ARG for other values or when the device cannot place
- * such a cluster with this batch's shared memory. */
+/* Thread blocks per member for the batch's solves, the same for every member:
+ * 1 gives every member one thread block, so that up to one member per SM run
+ * at once; 2, 4, 8 or 16 give every member a thread-block cluster of that many
+ * blocks (one per SM, cluster barriers and partial sums through distributed
+ * shared memory), which shortens large members at the cost of fewer members
+ * at once.  Replaces a split (sw_batch_set_split).  SW_ERR_BAD_ARG for other
+ * values or when the device cannot place such a cluster with this batch's
+ * shared memory.
+ *
+ * The default set by sw_create_batch is the launch shape with the shortest
+ * modelled makespan (a member's time taken as its unknowns over the SMs of
+ * its team times a per-SM efficiency measured for each cluster size): one
+ * block for every member, clusters of one size for every member, or a split
+ * (sw_batch_set_split). */
 int sw_batch_set_cluster(sw_batch *b, int blocks_per_member);
+/* Split launch: the n_big largest members (by unknowns) on clusters of
+ * blocks_per_member (2, 4, 8 or 16) blocks, the other n - n_big on one block
+ * each, the two launches side by side (the single-block one on a stream of
+ * the batch, joined back to the caller's stream by events).  Each big member
+ * gets a cluster of its own where the device can place that many clusters
+ * beside at least one single block; the single blocks take the remaining SMs.
+ * SW_ERR_BAD_ARG unless 1 <= n_big < n and the device can place such a
+ * cluster. */
+int sw_batch_set_split(sw_batch *b, int n_big, int blocks_per_member);
+/* The batch's launch shape: members on clusters, blocks per cluster member,
+ * blocks of the cluster launch, blocks of the single-block launch. */
+int sw_batch_get_launch(sw_batch *b, int *n_big, int *blocks_per_member, int *cluster_blocks, int *single_blocks);
+/* Tile autotuner of the batch: sw_create_batch times the operator apply of
+ * every member at once (one block per member, the inner precision) with tiles
+ * of 8, 16, 32 and 64 columns (each cut to the largest width that divides the
+ * member's nx) and keeps the fastest for the members' applies; the tile shape
+ * changes no output value.  *tile_x = the width kept; us[0..n) = microseconds
+ * per batched apply for each candidate (n <= 4 values written, 0 where not
+ * timed). */
+int sw_batch_autotuned_tile(sw_batch *b, int *tile_x, double *us, int n);
 /* One Runge-Kutta stage of every member (each needs its state and physics set).
  * Relaxation zones set with sw_set_relaxation are not applied here. */
 int sw_batch_advance_stage(sw_batch *b, void *stream);

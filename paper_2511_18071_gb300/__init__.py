@@ -107,6 +107,9 @@ def lib():
         L.sw_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sw_batch_advance_stage.argtypes = [vp, vp]
         L.sw_batch_set_cluster.argtypes = [vp, ip]
+        L.sw_batch_set_split.argtypes = [vp, ip, ip]
+        L.sw_batch_get_launch.argtypes = [vp, C.POINTER(ip), C.POINTER(ip), C.POINTER(ip), C.POINTER(ip)]
+        L.sw_batch_autotuned_tile.argtypes = [vp, C.POINTER(ip), vp, ip]
         L.sw_get_solve_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
         L.sw_test_stall_exchange.argtypes = [vp, ip]
         L.sw_profile_kernels.argtypes = [vp, ip, vp, ip]
@@ -119,7 +122,7 @@ def lib():
                      "sw_set_state", "sw_get_state", "sw_advance_stage", "sw_enable_timing", "sw_get_solve_time",
                      "sw_get_last_system", "sw_apply_operator_noalloc", "sw_get_phase_times", "sw_create_batch",
                      "sw_destroy_batch", "sw_batch_solve", "sw_batch_advance_stage", "sw_batch_set_cluster", "sw_set_relaxation",
-                     "sw_set_step"]:
+                     "sw_set_step", "sw_batch_set_split", "sw_batch_get_launch", "sw_batch_autotuned_tile"]:
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -367,6 +370,24 @@ class Batch:
     def set_cluster(self, blocks_per_member):
         """Thread blocks per member (1, or a cluster of 2, 4, 8, 16)."""
         return _check(lib().sw_batch_set_cluster(self.handle, int(blocks_per_member)))
+
+    def set_split(self, n_big, blocks_per_member):
+        """The n_big largest members on clusters of blocks_per_member, the rest one block each."""
+        return _check(lib().sw_batch_set_split(self.handle, int(n_big), int(blocks_per_member)))
+
+    def autotuned_tile(self):
+        """(tile width kept, {candidate width: microseconds per batched apply})."""
+        import numpy as np
+        tx = C.c_int()
+        us = np.zeros(4)
+        _check(lib().sw_batch_autotuned_tile(self.handle, C.byref(tx), C.c_void_p(us.ctypes.data), 4))
+        return tx.value, dict(zip((8, 16, 32, 64), us.tolist()))
+
+    def launch_shape(self):
+        """(members on clusters, blocks per cluster member, cluster-launch blocks, single-block-launch blocks)."""
+        v = [C.c_int() for _ in range(4)]
+        _check(lib().sw_batch_get_launch(self.handle, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def advance_stage(self, stream=None):
         return batch_advance_stage(self.handle, stream)

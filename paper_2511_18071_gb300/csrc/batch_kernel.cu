@@ -16,8 +16,6 @@
 
 namespace sw {
 
-constexpr int BATCH_WM = WM_ANYWALL | WM_2D;
-
 template <typename TI>
 __global__ void __launch_bounds__(NTHREADS, 1) batch_solve_kernel(const BatchItem *items, int n, int *counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -17,6 +17,8 @@
 // host enqueues a whole restart cycle and synchronises once per cycle.
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <utility>
 #include <vector>
 
@@ -862,6 +864,32 @@ static Tiling tune_tiles(Problem *P) {
     return best;
 }
 
+// Write the constant-memory sigma weights of the column form for P's number of
+// levels (once per device and P; every problem with those levels has the same
+// weights, so a later write would store the same values).
+static cudaError_t colapply_set_weights(const Problem *P) {
+    static std::mutex mu;
+    static std::set<std::pair<int, int>> done;
+    const int nl = P->dev.P;
+    if (nl != 10 && nl != 18 && nl != 34) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({dev, nl})) return cudaSuccess;
+    double wx1[W], wx2[W], wy1[W], wy2[W];
+    std::vector<double> ws(2 * (size_t)nl * W);
+    std::vector<int> win(nl);
+    grid_weights(P->grid, wx1, wx2, wy1, wy2, ws.data(), ws.data() + (size_t)nl * W, win.data());
+    std::vector<float> ws32(ws.begin(), ws.end());
+    const int off = nl == 10 ? colw_off<10>() : (nl == 18 ? colw_off<18>() : colw_off<34>());
+    e = cudaMemcpyToSymbol(c_colw64, ws.data(), ws.size() * sizeof(double), off * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(c_colw32, ws32.data(), ws32.size() * sizeof(float), off * sizeof(float));
+    if (e == cudaSuccess) done.insert({dev, nl});
+    return e;
+}
+
 int setup_streamed(Problem *P) {
     Streamed *S = new (std::nothrow) Streamed();
     if (!S) { set_error("out of host memory"); return SW_ERR_BAD_ARG; }
@@ -876,6 +904,7 @@ int setup_streamed(Problem *P) {
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->partB, (size_t)SNB * PART_STRIDE * sizeof(double));
     if (e == cudaSuccess) P->allocs.push_back(S->partB);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_done, sizeof(int));
+    if (e == cudaSuccess && !D.walls) e = colapply_set_weights(P);
     if (e != cudaSuccess) return cuda_fail(e, "streamed executor set-up");
     {
         const bool f32 = P->params.precision == SW_PRECISION_MIXED;

@@ -4,6 +4,9 @@
 
 namespace sw {
 
+// batch members: any mix of periodic and walled two-dimensional grids
+constexpr int BATCH_WM = WM_ANYWALL | WM_2D;
+
 constexpr size_t BSMEM_FIXED = (sizeof(SmemFixed) + 255) & ~size_t(255);
 
 struct BatchItem {

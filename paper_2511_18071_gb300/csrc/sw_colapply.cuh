@@ -6,7 +6,8 @@
 // are staged in shared memory plane by plane (coalesced rows along x); each
 // thread then computes D_sigma p for its own column and for at most one halo
 // column, with the column's P values in registers (the sigma windows are
-// compile-time: clamp(l - 3, 0, P - 7)), writes it to shared memory, and
+// compile-time: clamp(l - 3, 0, P - 7); the sigma weights in constant
+// memory), writes it to shared memory, and
 // finally forms the rows of its own column: x and y neighbours from shared
 // memory, the sigma terms and its own D_sigma p from registers, the column's
 // transform coefficients loaded once for all levels.  The arithmetic is that
@@ -15,6 +16,25 @@
 #include "sw_device.cuh"
 
 namespace sw {
+
+// The sigma weights of the column form live in constant memory, one table per
+// precision and number of levels: on the uniform sigma grid they depend on P
+// alone, so every problem with P levels writes the same values (at set-up,
+// before the first launch that reads them; colapply_set_weights).  With the
+// level and window position known at compile time, the multiply-adds take
+// them as constant-bank operands instead of loading them from shared memory.
+// Layout per P: first derivative P x W, then second derivative P x W.
+__constant__ float c_colw32[2 * (10 + 18 + 34) * W];
+__constant__ double c_colw64[2 * (10 + 18 + 34) * W];
+
+template <int P>
+__host__ __device__ constexpr int colw_off() { return P == 10 ? 0 : (P == 18 ? 2 * 10 * W : 2 * (10 + 18) * W); }
+
+template <typename T, int P>
+__device__ __forceinline__ T colw(int d, int l, int k) {
+    if constexpr (sizeof(T) == 8) return c_colw64[colw_off<P>() + d * P * W + l * W + k];
+    else return c_colw32[colw_off<P>() + d * P * W + l * W + k];
+}
 
 template <bool TD> struct ColShape;
 template <> struct ColShape<true> { static constexpr int CX = 32, CY = 8; };    // 3-D: 32 x 8 columns
@@ -30,7 +50,7 @@ struct ColGeom {
     // corners are never read.  At most one per thread.
     static constexpr int NHALO = TD ? 2 * HALF * CX + 2 * HALF * CY : 2 * HALF;
     static_assert(NHALO <= CX * CY, "one halo column per thread");
-    static constexpr size_t smem() { return (2 * (size_t)HW * P + 2 * (size_t)P * W) * sizeof(T); }
+    static constexpr size_t smem() { return 2 * (size_t)HW * P * sizeof(T); }
 };
 
 // whether the column-marching operator serves this grid
@@ -46,20 +66,10 @@ __device__ inline void col_apply_tile(const Dev &D, int tile, unsigned char *sme
     constexpr int CX = G::CX, CY = G::CY, HX = G::HX, HW = G::HW;
     T *sp = reinterpret_cast<T *>(smem);
     T *sq = sp + (size_t)HW * P;
-    T *sw1 = sq + (size_t)HW * P;
-    T *sw2 = sw1 + P * W;
     const int tid = threadIdx.x;
     const int ntx = D.nx / CX;
     const int tx0 = (tile % ntx) * CX, ty0 = (tile / ntx) * CY;
     const int n = D.ncol;
-    // sigma weights of every level
-    {
-        const T *w1 = Prec<T>::ws1(D), *w2 = Prec<T>::ws2(D);
-        for (int i = tid; i < P * W; i += CX * CY) {
-            sw1[i] = w1[i];
-            sw2[i] = w2[i];
-        }
-    }
     // positions of this thread: its own column, then at most one halo column
     const int txo = tid % CX, tyo = tid / CX;
     const int own = (tyo + (TD ? HALF : 0)) * HX + txo + HALF;
@@ -109,8 +119,8 @@ __device__ inline void col_apply_tile(const Dev &D, int tile, unsigned char *sme
         T a = T(0), b = T(0);
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            a += sw1[l * W + k] * pc[s0 + k];
-            if (hpos >= 0) b += sw1[l * W + k] * ph[s0 + k];
+            a += colw<T, P>(0, l, k) * pc[s0 + k];
+            if (hpos >= 0) b += colw<T, P>(0, l, k) * ph[s0 + k];
         }
         qc[l] = a;
         sq[l * HW + own] = a;
@@ -180,7 +190,7 @@ __device__ inline void col_apply_tile(const Dev &D, int tile, unsigned char *sme
             const int s0 = l - HALF < 0 ? 0 : (l - HALF > LAST ? LAST : l - HALF);
             T pss = T(0);
 #pragma unroll
-            for (int k = 0; k < W; ++k) pss += sw2[l * W + k] * pc[s0 + k];
+            for (int k = 0; k < W; ++k) pss += colw<T, P>(1, l, k) * pc[s0 + k];
             y = pxx + c_xs * pxs + c_s * qc[l];
             if (TD) {
                 const T ay = ay0 - sg * ay1;

@@ -459,23 +459,57 @@ __device__ __forceinline__ T off_column_sum_walls(const Dev &D, const T *lu, con
 
 // sum over the off-column slots whose neighbour colour satisfies pick(colour)
 // CC >= 0 fixes the colour at compile time: the slot selection is then static
-// and every remaining load is unconditional, so they can all be in flight.
+// and every remaining load is unconditional.  With the colour known only at
+// run time the slots go in chunks (the seven levels of one neighbour column in
+// the box patterns, all slots of a cross pattern) whose loads are all issued
+// before the chunk's multiply-adds, so they are in flight together instead of
+// one slot's pair at a time.  The products are added in slot order either way.
 template <int L, typename T, bool LOWER, int CC = -1>
 __device__ __forceinline__ T off_column_sum(const Dev &D, const T *lu, const T *vals, int c, int ix, int iy, int j,
                                             long long r) {
+    constexpr int N = Off<L>::N;
+    constexpr int CH = (L == BOX2D || L == BOX3D) ? 7 : N;
     const long long m = D.m;
     const int w0 = D.win[j + 1];
     const int cc = CC >= 0 ? CC : c;
     T acc = T(0);
+    if constexpr (CC >= 0) {
+        // static selection: one straight run of unconditional loads and adds
 #pragma unroll
-    for (int i = 0; i < Off<L>::N; ++i) {
-        const int ox = Off<L>::ox(i), oy = Off<L>::oy(i);
-        const int nc = (cc + ox + oy) & 3;
-        if (LOWER ? (nc >= cc) : (nc <= cc)) continue;
-        const int lev = Off<L>::kk(i) < 0 ? j : w0 + Off<L>::kk(i);
-        const int gx = wrapi(ix + ox, D.nx);
-        const int gy = (L == CROSS3D || L == BOX3D) ? wrapi(iy + oy, D.ny) : 0;
-        acc += lu[(long long)Off<L>::slot(i) * m + r] * vals[(long long)(lev + 1) * D.ncol + gy * D.nx + gx];
+        for (int i = 0; i < N; ++i) {
+            const int ox = Off<L>::ox(i), oy = Off<L>::oy(i);
+            const int nc = (cc + ox + oy) & 3;
+            if (LOWER ? (nc >= cc) : (nc <= cc)) continue;
+            const int lev = Off<L>::kk(i) < 0 ? j : w0 + Off<L>::kk(i);
+            const int gx = wrapi(ix + ox, D.nx);
+            const int gy = (L == CROSS3D || L == BOX3D) ? wrapi(iy + oy, D.ny) : 0;
+            acc += lu[(long long)Off<L>::slot(i) * m + r] * vals[(long long)(lev + 1) * D.ncol + gy * D.nx + gx];
+        }
+        return acc;
+    }
+#pragma unroll
+    for (int i0 = 0; i0 < N; i0 += CH) {
+        T a[CH], b[CH];
+        bool on[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int i = i0 + u;
+            const int ox = Off<L>::ox(i), oy = Off<L>::oy(i);
+            const int nc = (cc + ox + oy) & 3;
+            on[u] = LOWER ? (nc < cc) : (nc > cc);
+            a[u] = T(0);
+            b[u] = T(0);
+            if (on[u]) {
+                const int lev = Off<L>::kk(i) < 0 ? j : w0 + Off<L>::kk(i);
+                const int gx = wrapi(ix + ox, D.nx);
+                const int gy = (L == CROSS3D || L == BOX3D) ? wrapi(iy + oy, D.ny) : 0;
+                a[u] = lu[(long long)Off<L>::slot(i) * m + r];
+                b[u] = vals[(long long)(lev + 1) * D.ncol + gy * D.nx + gx];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (on[u]) acc += a[u] * b[u];
     }
     return acc;
 }
@@ -526,25 +560,30 @@ __device__ __forceinline__ void column_block_product(const T *bt, const T (&g)[2
 }
 template <typename T>
 __device__ __forceinline__ void column_block_product_two(const T *bt, const T (&g)[2], T (&y)[2], int P, int lane) {
+    // two levels per lane (lane and lane + 32); rows loaded eight at a time
+    // as in the one-level form, even rows summed in a0 and odd rows in a1
     T a0[2] = {T(0), T(0)}, a1[2] = {T(0), T(0)};
     const int a_h[2] = {lane, lane + 32};
-    int a2 = 0;
-    for (; a2 + 1 < P; a2 += 2) {
-        const T g0 = __shfl_sync(0xffffffffu, (a2 >> 5) ? g[1] : g[0], a2 & 31);
-        const T g1 = __shfl_sync(0xffffffffu, ((a2 + 1) >> 5) ? g[1] : g[0], (a2 + 1) & 31);
+    for (int a2 = 0; a2 < P; a2 += 8) {
+        T b8[2][8];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (a_h[h] < P) {
-                a0[h] += bt[a2 * P + a_h[h]] * g0;
-                a1[h] += bt[(a2 + 1) * P + a_h[h]] * g1;
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) b8[h][u] = (a_h[h] < P && a2 + u < P) ? bt[(a2 + u) * P + a_h[h]] : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            if (a2 + u >= P) break;
+            const int r0 = a2 + u, r1 = a2 + u + 1;
+            const T g0 = __shfl_sync(0xffffffffu, (r0 >> 5) ? g[1] : g[0], r0 & 31);
+            const T g1 = __shfl_sync(0xffffffffu, (r1 < P && (r1 >> 5)) ? g[1] : g[0], r1 & 31);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (a_h[h] < P) {
+                    a0[h] += b8[h][u] * g0;
+                    if (r1 < P) a1[h] += b8[h][u + 1] * g1;
+                }
             }
         }
-    }
-    if (a2 < P) {
-        const T g0 = __shfl_sync(0xffffffffu, (a2 >> 5) ? g[1] : g[0], a2 & 31);
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-            if (a_h[h] < P) a0[h] += bt[a2 * P + a_h[h]] * g0;
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) y[h] = a0[h] + a1[h];

@@ -47,14 +47,21 @@ def _surfaces(nx, seed):
     return e1, e1 + 0.002 * np.cos(3 * x + rng.uniform(0, 6))
 
 
-@pytest.mark.parametrize("cluster", [1, 4])
+@pytest.mark.parametrize("cluster", [1, 4, "split"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_batch_solve_matches_oracle(sw, precision, cluster):
     kw = dict(restart=20, max_restarts=400, tol=1e-12, guess="cold")
     mem = _members()
     probs = [sw.Problem(nx, 1, nz, L, 0.0, h, precision=precision, **kw) for nx, nz, L, h in mem]
     batch = sw.Batch(probs)
-    batch.set_cluster(cluster)
+    if cluster == "split":
+        # the two largest members on 4-block clusters, the other three on single
+        # blocks, both launches side by side
+        batch.set_split(2, 4)
+        nb, cs, cblocks, sblocks = batch.launch_shape()
+        assert (nb, cs) == (2, 4) and cblocks % 4 == 0 and cblocks >= 4 and sblocks >= 1
+    else:
+        batch.set_cluster(cluster)
     eps, ecs, bs, xs, refs = [], [], [], [], []
     for i, (nx, nz, L, h) in enumerate(mem):
         ora = O.OracleProblem(nx, 1, nz, L, 0.0, h, **kw)
@@ -66,6 +73,9 @@ def test_batch_solve_matches_oracle(sw, precision, cluster):
         refs.append(xo)
         eps.append(_t(e1)); ecs.append(_t(e2)); bs.append(_t(b))
         xs.append(torch.zeros(ora.m, dtype=torch.float64, device=DEV))
+    # the tile autotuner timed every candidate width and kept one of them
+    tx, us = batch.autotuned_tile()
+    assert tx in us and all(v > 0 for v in us.values()) and us[tx] == min(us.values()), (tx, us)
     batch.solve(eps, ecs, bs, xs)
     torch.cuda.synchronize()
     for i, p in enumerate(probs):
@@ -152,6 +162,9 @@ def test_batch512_one_launch_sampled_parity(sw):
         sw.set_physics(p.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
         sw.set_state(p.handle, _t(wl["u"]), None, _t(wl["w"]), _t(wl["eta"]))
     batch = sw.Batch(probs)
+    # the default launch of this batch (the makespan model): clusters for every member
+    nb, cs, cblocks, sblocks = batch.launch_shape()
+    assert nb == len(members) and cs >= 2 and cblocks % cs == 0 and cblocks >= cs, batch.launch_shape()
     batch.advance_stage()
     torch.cuda.synchronize()
     bad = [(i, members[i]["name"], p.stats()) for i, p in enumerate(probs) if p.stats()["status"] != 0]
