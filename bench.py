@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline-large", action="store_true")
     ap.add_argument("--n3d-roof", type=int, default=512, help="roofline_large: nx = ny of the 3-D field")
+    ap.add_argument("--n2d-roof", type=int, default=65536, help="roofline_large: nx of the 2-D field (33 levels)")
     ap.add_argument("--members", type=int, default=512, help="batch512: number of instances")
     ap.add_argument("--batch-budget", type=float, default=240.0, help="batch512: seconds per phase at most")
     ap.add_argument("--clusters", default="auto",
@@ -446,6 +447,7 @@ def gpu_arm(args, rank, world, local_rank):
     if not args.no_roofline_large:
         try:
             roof_large = roofline_large(sw, torch, dev, args.n3d_roof, peaks)
+            roof_large["2d"] = roofline_large(sw, torch, dev, None, peaks, nx2d=args.n2d_roof)
         except sw.SawaveError as err:
             roof_large = {"unavailable": str(err)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -469,22 +471,29 @@ def gpu_arm(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def roofline_large(sw, torch, dev, n3d, peaks):
-    """Per-kernel roofline of the streamed executor at a bandwidth size: the
-    3-D field (n3d x n3d x 17, bumps, 16 directional components) in the
+def roofline_large(sw, torch, dev, n3d, peaks, nx2d=None):
+    """Per-kernel roofline of the streamed executor at a bandwidth size, in the
     precision form, two stage solves, then the hot kernels of an Arnoldi step
     timed alone (sw_profile_kernels: CUDA events, L2 written between launches).
-    Algorithmic bytes and flops per launch follow the method's counts per point
-    (FP32 inner vectors and factors; m unknowns, ncol columns, P levels, s
-    factor slots per row, 84 of them off-column)."""
+    The workload is the 3-D field (n3d x n3d x 17, bumps, 16 directional
+    components) or, with nx2d, a 2-D Airy field nx2d x 33 spanning nx2d / 128
+    wavelengths.  Algorithmic bytes and flops per launch follow the method's
+    counts per point (FP32 inner vectors and factors; m unknowns, ncol columns,
+    P levels, `off` factor slots per row off the column, half of them read per
+    sweep; the in-column parts as P x P inverse blocks)."""
     import workloads as W
-    wl = W.bumpy_3d(nx=n3d, ny=n3d)
+    if nx2d:
+        wl = W.airy_2d(nx=nx2d, nz=33, kh=1.0, a_over_h=0.02, waves=max(1, nx2d // 128))
+        ly, v = 0.0, None
+    else:
+        wl = W.bumpy_3d(nx=n3d, ny=n3d)
+        ly = wl["ly"]
     t0 = time.perf_counter()
-    P = sw.Problem(wl["nx"], wl["ny"], wl["nz"], wl["lx"], wl["ly"], wl["h"], precision="mixed", executor="streamed",
+    P = sw.Problem(wl["nx"], wl["ny"], wl["nz"], wl["lx"], ly, wl["h"], precision="mixed", executor="streamed",
                    restart=20, max_restarts=500, tol=1e-8, guess="ewma", k=10, decay=0.9, n_init_solves=30, seed=2511)
     create_s = time.perf_counter() - t0
     sw.set_physics(P.handle, sw.Physics(wl["g"], wl["rho"], wl["dt"]))
-    t = lambda a: torch.tensor(a, device=dev)
+    t = lambda a: None if a is None else torch.tensor(a, device=dev)
     sw.set_state(P.handle, t(wl["u"]), t(wl["v"]), t(wl["w"]), t(wl["eta"]))
     for _ in range(2):
         sw.advance_stage(P.handle)
@@ -493,18 +502,24 @@ def roofline_large(sw, torch, dev, n3d, peaks):
     us = sw.profile_kernels(P.handle, reps=5)
     col, tx, ty = sw.autotuned_apply(P.handle)
     P.close()
-    m, ncol, Pl, s_slots, off = wl["m"], wl["nx"] * wl["ny"], wl["nz"] + 1, 91, 84
+    m, ncol, Pl = wl["m"], wl["nx"] * wl["ny"], wl["nz"] + 1
+    if nx2d:   # flat 2-D bed: 6 factor slots off the column; 12 coefficient arrays
+        off, fA, ncoef = 6, 76.0, 12
+    else:      # varying 3-D bed: 84 factor slots off the column
+        off, fA, ncoef = 84, 123.0, 16
     j = 10
     model = {   # bytes, flops per launch (class of launches)
-        "apply": (8.0 * m + 4.0 * 16 * ncol, 123.0 * m, "alu"),
+        "apply": (8.0 * m + 4.0 * ncoef * ncol, fA * m, "alu"),
         "ilu_gather_fwd": (4.0 * (off / 2) * m + 8.0 * m, 2.0 * (off / 2) * m, "hbm"),
         "ilu_products": (2.0 * 4 * Pl * Pl * ncol + 16.0 * m, 4.0 * Pl * m, "hbm"),
         "ilu_gather_bwd": (4.0 * (off / 2) * m + 6.0 * m, 2.0 * (off / 2) * m, "hbm"),
         "cgs_pass1_j10": (4.0 * (j + 2) * m, 2.0 * (j + 1) * m, "hbm"),
         "cgs_pass2_j10": (4.0 * (j + 3) * m, 4.0 * (j + 1) * m, "hbm"),
         "cgs_pass3_j10": (4.0 * (j + 3) * m, 2.0 * (j + 1) * m + 2.0 * m, "hbm"),
-        "ilu_application": ((4.0 * (s_slots + 1) + 16.0) * m, (2.0 * s_slots - 1) * m, "hbm"),
     }
+    # the whole application: both gathers and both block-product sweeps
+    model["ilu_application"] = (sum(model[k][0] for k in ("ilu_gather_fwd", "ilu_products", "ilu_gather_bwd")),
+                                sum(model[k][1] for k in ("ilu_gather_fwd", "ilu_products", "ilu_gather_bwd")), "hbm")
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sm_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     hbm = peaks.get("hbm_gbs")
@@ -517,7 +532,8 @@ def roofline_large(sw, torch, dev, n3d, peaks):
         kern[k] = {"us_per_launch": v, "alg_bytes": b, "alg_flops": f, "gbs": gbs, "tflops": tfs, "bound": bound,
                    "frac": frac}
     dom = max((k for k in kern if k != "ilu_application"), key=lambda k: kern[k]["us_per_launch"])
-    return {"workload": "bumpy3d_%dx%dx17" % (n3d, n3d), "unknowns": m, "precision": "mixed (FP32 inner)",
+    name = ("airy2d_%dx33_%dwaves" % (nx2d, max(1, nx2d // 128))) if nx2d else "bumpy3d_%dx%dx17" % (n3d, n3d)
+    return {"workload": name, "unknowns": m, "precision": "mixed (FP32 inner)",
             "executor": "streamed", "create_s": create_s, "solves": 2, "iters_last_solve": st["iterations"],
             "apply_form": {"column_marching": bool(col), "tile": [tx, ty]},
             "peaks": {"hbm_gbs": hbm, "hbm_source": "measured copy (MEASURED_PEAKS.json)",
@@ -669,9 +685,14 @@ def bumpy3d_arm(args):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "iters_per_solve": mx["iters_per_solve"],
             "fp64": res["fp64"], "mixed": mx, "speedup_vs_fp64": mx["value"] / res["fp64"]["value"],
             "mixed_vs_fp64_rel_error_tol1e-10": err,
-            "roofline": {"kernel": "solve_kernel<float>", "bound": "hbm", "achieved": ach,
+            "roofline": {"kernel": "whole precision-form solve (%s executor, every kernel of the solve)"
+                                   % (args.executor if args.executor != "auto"
+                                      else ("streamed" if wl["m"] > 262144 else "persistent")),
+                         "bound": "hbm", "achieved": ach,
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                         "frac": ach / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None, "traffic": None},
+                         "frac": ach / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None, "traffic": None,
+                         "note": "model bytes of the solves over their kernel time; per-kernel fractions are in "
+                                 "the headline line's roofline_large"},
             "config": {"workload": "bumpy3d_%dx%dx17" % (args.n3d, args.n3d), "unknowns": wl["m"], "guess": "ewma",
                        "k": args.k,
                        "executor": args.executor,

@@ -92,16 +92,21 @@ __global__ void __launch_bounds__(NTHREADS) sk_apply_vj(Dev D, Tiling tl, const 
 }
 
 // The same apply in column-marching form (periodic grids with 10, 18 or 34
-// levels; sw_colapply.cuh), one CX x CY tile per block.
+// levels; sw_colapply.cuh), one CX x CY tile per block.  Up to 18 levels in
+// FP32 the kernel is held to 80 registers, three blocks per SM: 28.3 us per
+// launch on the 512^2 x 17 field against 31.4 us at two blocks (128
+// registers) and 31.1 us at four (64 registers, with spills).
 template <typename TI, int P, bool TD>
-__global__ void __launch_bounds__(NTHREADS, (P <= 18 ? 2 : 1))
-    sk_apply_col(Dev D, const TI *V, int j, const SState *ss, TI *t) {
+__global__ void __launch_bounds__(NTHREADS, (P > 18 ? (sizeof(TI) == 4 ? 2 : 1) : (sizeof(TI) == 4 ? 3 : 2)))
+    sk_apply_col(Dev D, ColXY<TI> xy, const TI *V, int j, const SState *ss, TI *t) {
     if (ss->stop || ss->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LdVec<TI, TI> ld{V + (size_t)j * D.m, TI(ss->scale[j])};
     StVec<TI, TI> st{t};
-    col_apply_tile<TI, P, TD>(D, blockIdx.x, smem_raw, ld, st);
+    col_apply_tile<TI, P, TD>(D, xy, blockIdx.x, smem_raw, ld, st);
 }
+
+
 
 template <typename TI, int P, bool TD>
 static const void *col_kernel() { return (const void *)sk_apply_col<TI, P, TD>; }
@@ -124,14 +129,19 @@ static bool col_launch_shape(const Dev &D, const void **k, int *grid, size_t *sm
     return *smem <= 227 * 1024;
 }
 
+struct Streamed;
+template <typename TI> static const ColXY<TI> &xy_of(const Streamed *S);
+
 template <typename TI>
-static cudaError_t launch_col(const Dev &D, const TI *V, int j, const SState *ss, TI *t, cudaStream_t s) {
+static cudaError_t launch_col(const Problem *P, const TI *V, int j, const SState *ss, TI *t, cudaStream_t s) {
+    const Dev &D = P->dev;
     const void *k = nullptr;
     int grid = 0;
     size_t smem = 0;
     if (!col_launch_shape<TI>(D, &k, &grid, &smem)) return cudaErrorInvalidValue;
     Dev Dc = D;
-    void *args[] = {&Dc, (void *)&V, &j, (void *)&ss, &t};
+    ColXY<TI> xy = xy_of<TI>((const Streamed *)P->streamed);
+    void *args[] = {&Dc, &xy, (void *)&V, &j, (void *)&ss, &t};
     return cudaLaunchKernel(k, dim3(grid), dim3(NTHREADS), args, smem, s);
 }
 
@@ -743,7 +753,12 @@ struct Streamed {
     int *h_done = nullptr;                       // pinned flag read once per cycle
     Tiling tl{};
     int nbA = 0;
+    ColXY<float> xy32{};                         // x / y weights of the column-marching apply
+    ColXY<double> xy64{};
 };
+
+template <> const ColXY<float> &xy_of<float>(const Streamed *S) { return S->xy32; }
+template <> const ColXY<double> &xy_of<double>(const Streamed *S) { return S->xy64; }
 
 static Tiling st_tiling(const Dev &D) {
     // as for the standalone operator: at least 304 tiles, at most 64 columns wide
@@ -845,9 +860,9 @@ static Tiling tune_tiles(Problem *P) {
         size_t smc = 0;
         if (WM == 0 && col_launch_shape<TI>(D, &k, &grid, &smc) &&
             ensure_smem((const void *)k, (size_t)(int)smc) == cudaSuccess) {
-            bool ok = launch_col<TI>(D, V, 0, S->ss, tw, cs) == cudaSuccess;
+            bool ok = launch_col<TI>(P, V, 0, S->ss, tw, cs) == cudaSuccess;
             ok = ok && cudaEventRecord(a, cs) == cudaSuccess;
-            for (int r = 0; r < 3 && ok; ++r) ok = launch_col<TI>(D, V, 0, S->ss, tw, cs) == cudaSuccess;
+            for (int r = 0; r < 3 && ok; ++r) ok = launch_col<TI>(P, V, 0, S->ss, tw, cs) == cudaSuccess;
             ok = ok && cudaEventRecord(b, cs) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess;
             float ms = 0.f;
             if (ok && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
@@ -905,6 +920,17 @@ int setup_streamed(Problem *P) {
     if (e == cudaSuccess) P->allocs.push_back(S->partB);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_done, sizeof(int));
     if (e == cudaSuccess && !D.walls) e = colapply_set_weights(P);
+    {
+        double wx1[W], wx2[W], wy1[W], wy2[W];
+        std::vector<double> ws(2 * (size_t)D.P * W);
+        std::vector<int> win(D.P);
+        grid_weights(P->grid, wx1, wx2, wy1, wy2, ws.data(), ws.data() + (size_t)D.P * W, win.data());
+        for (int t = 0; t < W; ++t) {
+            S->xy64.wx1[t] = wx1[t]; S->xy64.wx2[t] = wx2[t]; S->xy64.wy1[t] = wy1[t]; S->xy64.wy2[t] = wy2[t];
+            S->xy32.wx1[t] = (float)wx1[t]; S->xy32.wx2[t] = (float)wx2[t];
+            S->xy32.wy1[t] = (float)wy1[t]; S->xy32.wy2[t] = (float)wy2[t];
+        }
+    }
     if (e != cudaSuccess) return cuda_fail(e, "streamed executor set-up");
     {
         const bool f32 = P->params.precision == SW_PRECISION_MIXED;
@@ -968,7 +994,7 @@ static long long enqueue_cycle(const Problem *P, TI *V, TI *tw, SState *ss, doub
     long long n = 0;
     for (int j = 0; j < P->params.restart; ++j) {
         TI *w = V + (size_t)(j + 1) * m;
-        if (S->col) launch_col<TI>(D, V, j, ss, tw, s);
+        if (S->col) launch_col<TI>(P, V, j, ss, tw, s);
         else sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, j, ss, tw);
         st_ilu<TI, TI, WM>(P, tw, w, ss, 1, s);
         launch_cgs<TI, 1>(V, j, w, m, ss, partB, s);
@@ -1194,7 +1220,7 @@ static int profile_streamed(Problem *P, int reps, double *us, int n) {
     const int ng = D.ngroups;
     double t[8];
     t[0] = time_launches(s, flush, fb, reps, [&] {
-        if (S->col) launch_col<TI>(D, V, 0, S->ss, tw, s);
+        if (S->col) launch_col<TI>(P, V, 0, S->ss, tw, s);
         else sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, 0, S->ss, tw);
     });
     t[1] = time_launches(s, flush, fb, reps, [&] {

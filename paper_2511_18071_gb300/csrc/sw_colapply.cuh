@@ -4,14 +4,16 @@
 //
 // One thread per column of a CX x CY tile.  The tile and its three-column halo
 // are staged in shared memory plane by plane (coalesced rows along x); each
-// thread then computes D_sigma p for its own column and for at most one halo
-// column, with the column's P values in registers (the sigma windows are
-// compile-time: clamp(l - 3, 0, P - 7); the sigma weights in constant
-// memory), writes it to shared memory, and
-// finally forms the rows of its own column: x and y neighbours from shared
-// memory, the sigma terms and its own D_sigma p from registers, the column's
-// transform coefficients loaded once for all levels.  The arithmetic is that
-// of apply_tile_t (sw_device.cuh), term by term in the same order.
+// thread keeps its own column's P values in registers.  It then marches up
+// its column: at level m it forms D_x p and D_xx p (and D_y p, D_yy p) from
+// the six neighbours in shared memory, and finishes every row whose sigma
+// window (compile-time: clamp(l - 3, 0, P - 7)) ends at m.  The sigma
+// derivatives are taken along the column from registers, with the sigma
+// weights as constant-memory operands; the mixed derivatives D_x D_sigma p
+// are formed as D_sigma (D_x p), the same tensor-product stencil applied in
+// the other order (equal in exact arithmetic, different rounding), so a level
+// needs twelve shared-memory loads and the tile one staging pass.  The row
+// formulas follow apply_tile_t (sw_device.cuh) term by term.
 #pragma once
 #include "sw_device.cuh"
 
@@ -36,6 +38,15 @@ __device__ __forceinline__ T colw(int d, int l, int k) {
     else return c_colw32[colw_off<P>() + d * P * W + l * W + k];
 }
 
+// The x and y weights of a problem, passed by value as a kernel argument (and
+// by value on to the tile routine: no address of it is ever taken, which would
+// make the compiler copy it to local memory): kernel arguments sit in a
+// constant bank, so the multiply-adds read them as operands.
+template <typename T>
+struct ColXY {
+    T wx1[W], wx2[W], wy1[W], wy2[W];
+};
+
 template <bool TD> struct ColShape;
 template <> struct ColShape<true> { static constexpr int CX = 32, CY = 8; };    // 3-D: 32 x 8 columns
 template <> struct ColShape<false> { static constexpr int CX = 256, CY = 1; };  // 2-D: 256 columns
@@ -50,7 +61,7 @@ struct ColGeom {
     // corners are never read.  At most one per thread.
     static constexpr int NHALO = TD ? 2 * HALF * CX + 2 * HALF * CY : 2 * HALF;
     static_assert(NHALO <= CX * CY, "one halo column per thread");
-    static constexpr size_t smem() { return 2 * (size_t)HW * P * sizeof(T); }
+    static constexpr size_t smem() { return (size_t)HW * P * sizeof(T); }
 };
 
 // whether the column-marching operator serves this grid
@@ -61,11 +72,11 @@ __host__ __device__ inline bool colapply_ok(const Dev &D, int P) {
 }
 
 template <typename T, int P, bool TD, class Loader, class Store>
-__device__ inline void col_apply_tile(const Dev &D, int tile, unsigned char *smem, Loader &ld, Store &st) {
+__device__ inline void col_apply_tile(const Dev &D, const ColXY<T> xy, int tile, unsigned char *smem, Loader &ld,
+                                      Store &st) {
     using G = ColGeom<T, P, TD>;
     constexpr int CX = G::CX, CY = G::CY, HX = G::HX, HW = G::HW;
     T *sp = reinterpret_cast<T *>(smem);
-    T *sq = sp + (size_t)HW * P;
     const int tid = threadIdx.x;
     const int ntx = D.nx / CX;
     const int tx0 = (tile % ntx) * CX, ty0 = (tile / ntx) * CY;
@@ -110,24 +121,7 @@ __device__ inline void col_apply_tile(const Dev &D, int tile, unsigned char *sme
         if (hpos >= 0) sp[l * HW + hpos] = ph[l];
     }
     __syncthreads();
-    // q = D_sigma p in registers (own column) and in shared memory (both)
-    T qc[P];
-#pragma unroll
-    for (int l = 0; l < P; ++l) {
-        constexpr int LAST = P - W;
-        const int s0 = l - HALF < 0 ? 0 : (l - HALF > LAST ? LAST : l - HALF);
-        T a = T(0), b = T(0);
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            a += colw<T, P>(0, l, k) * pc[s0 + k];
-            if (hpos >= 0) b += colw<T, P>(0, l, k) * ph[s0 + k];
-        }
-        qc[l] = a;
-        sq[l * HW + own] = a;
-        if (hpos >= 0) sq[l * HW + hpos] = b;
-    }
-    __syncthreads();
-    // rows of the own column
+    // the column's transform coefficients
     const T *cc = Prec<T>::cc(D);
     const T ap0 = cc[CC_AP0 * n + gco], ap1 = cc[CC_AP1 * n + gco];
     const T axp0 = cc[CC_AXP0 * n + gco], axp1 = cc[CC_AXP1 * n + gco];
@@ -144,34 +138,25 @@ __device__ inline void col_apply_tile(const Dev &D, int tile, unsigned char *sme
         by0 = cc[CC_BY0 * n + gco];
         by1 = cc[CC_BY1 * n + gco];
     }
-    T wx1[W], wx2[W], wy1[W], wy2[W];
-#pragma unroll
-    for (int t = 0; t < W; ++t) {
-        wx1[t] = Prec<T>::wx1(D)[t];
-        wx2[t] = Prec<T>::wx2(D)[t];
-        if (TD) {
-            wy1[t] = Prec<T>::wy1(D)[t];
-            wy2[t] = Prec<T>::wy2(D)[t];
-        }
-    }
     const T inv_nzm1 = T(1) / T(D.nz - 1);
-#pragma unroll
-    for (int l = 0; l < P; ++l) {
+    constexpr int LAST = P - W;
+    // Level by level, upwards: D_x p and D_xx p (and y) at level m from the
+    // six neighbours in shared memory; a row l is finished as soon as the
+    // last level of its sigma window is in, its mixed derivatives taken as
+    // D_sigma (D_x p) along the column (the tensor-product stencils commute).
+    T px[P] = {}, py[P] = {}, pxx[P] = {}, pyy[P] = {};
+    auto finish = [&](int l) {
+        const int s0 = l - HALF < 0 ? 0 : (l - HALF > LAST ? LAST : l - HALF);
         T y;
-        const T *pl = sp + l * HW + own;
-        const T *ql = sq + l * HW + own;
         if (l == P - 1) {
             y = pc[l];
         } else if (l == 0) {
-            const T *p1 = sp + HW + own;
-            T px = T(0), py = T(0);
+            T q1 = T(0);
+            constexpr int s1 = 1 - HALF < 0 ? 0 : (1 - HALF > LAST ? LAST : 1 - HALF);
 #pragma unroll
-            for (int t = -HALF; t <= HALF; ++t) {
-                px += wx1[t + HALF] * (t == 0 ? pc[1] : p1[t]);
-                if (TD) py += wy1[t + HALF] * (t == 0 ? pc[1] : p1[t * HX]);
-            }
-            y = gs * qc[1] + gxc * px;
-            if (TD) y += gyc * py;
+            for (int k = 0; k < W; ++k) q1 += colw<T, P>(0, 1, k) * pc[s1 + k];
+            y = gs * q1 + gxc * px[1];
+            if (TD) y += gyc * py[1];
         } else {
             const T sg = T(l - 1) * inv_nzm1;
             const T aa = ap0 - sg * ap1;
@@ -180,18 +165,14 @@ __device__ inline void col_apply_tile(const Dev &D, int tile, unsigned char *sme
             const T c_xs = aa + bb;
             T c_ss = aa * bb + ef;
             const T c_s = ax - bb * ap1;
-            T pxx = T(0), pxs = T(0);
+            T ql = T(0), pxs = T(0), pss = T(0);
 #pragma unroll
-            for (int t = -HALF; t <= HALF; ++t) {
-                pxx += wx2[t + HALF] * (t == 0 ? pc[l] : pl[t]);
-                pxs += wx1[t + HALF] * (t == 0 ? qc[l] : ql[t]);
+            for (int k = 0; k < W; ++k) {
+                ql += colw<T, P>(0, l, k) * pc[s0 + k];
+                pxs += colw<T, P>(0, l, k) * px[s0 + k];
+                pss += colw<T, P>(1, l, k) * pc[s0 + k];
             }
-            constexpr int LAST = P - W;
-            const int s0 = l - HALF < 0 ? 0 : (l - HALF > LAST ? LAST : l - HALF);
-            T pss = T(0);
-#pragma unroll
-            for (int k = 0; k < W; ++k) pss += colw<T, P>(1, l, k) * pc[s0 + k];
-            y = pxx + c_xs * pxs + c_s * qc[l];
+            y = pxx[l] + c_xs * pxs + c_s * ql;
             if (TD) {
                 const T ay = ay0 - sg * ay1;
                 const T by = by0 - sg * by1;
@@ -199,17 +180,48 @@ __device__ inline void col_apply_tile(const Dev &D, int tile, unsigned char *sme
                 c_ss += ay * by;
                 const T c_ys = ay + by;
                 const T c_sy = ayy - by * ay1;
-                T pyy = T(0), pys = T(0);
+                T pys = T(0);
 #pragma unroll
-                for (int t = -HALF; t <= HALF; ++t) {
-                    pyy += wy2[t + HALF] * (t == 0 ? pc[l] : pl[t * HX]);
-                    pys += wy1[t + HALF] * (t == 0 ? qc[l] : ql[t * HX]);
-                }
-                y += pyy + c_ys * pys + c_sy * qc[l];
+                for (int k = 0; k < W; ++k) pys += colw<T, P>(0, l, k) * py[s0 + k];
+                y += pyy[l] + c_ys * pys + c_sy * ql;
             }
             y += c_ss * pss;
         }
         st((long long)l * n + gco, y);
+    };
+#pragma unroll
+    for (int mlev = 0; mlev < P; ++mlev) {
+        const T *pl = sp + mlev * HW + own;
+        T a1 = T(0), a2 = T(0), b1 = T(0), b2 = T(0);
+#pragma unroll
+        for (int t = -HALF; t <= HALF; ++t) {
+            const T vx = t == 0 ? pc[mlev] : pl[t];
+            a1 += xy.wx1[t + HALF] * vx;
+            a2 += xy.wx2[t + HALF] * vx;
+            if (TD) {
+                const T vy = t == 0 ? pc[mlev] : pl[t * HX];
+                b1 += xy.wy1[t + HALF] * vy;
+                b2 += xy.wy2[t + HALF] * vy;
+            }
+        }
+        px[mlev] = a1;
+        pxx[mlev] = a2;
+        py[mlev] = b1;
+        pyy[mlev] = b2;
+        // rows whose window ends at this level: the surface row at once, the
+        // ghost row with D_x p of level 1, rows 1..3 (window 0..6) at level 6,
+        // interior rows l at l + 3, rows P-4..P-2 (window P-7..P-1) at the top
+        if (mlev == 0) finish(P - 1);
+        if (mlev == 1) finish(0);
+        if (mlev == W - 1) {
+#pragma unroll
+            for (int l = 1; l <= HALF; ++l) finish(l);
+        }
+        if (mlev >= W && mlev <= P - 2) finish(mlev - HALF);
+        if (mlev == P - 1) {
+#pragma unroll
+            for (int l = P - 1 - HALF; l <= P - 2; ++l) finish(l);
+        }
     }
     __syncthreads();
 }

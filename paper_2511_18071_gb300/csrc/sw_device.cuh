@@ -485,31 +485,31 @@ __device__ __forceinline__ T off_column_sum(const Dev &D, const T *lu, const T *
             const int gy = (L == CROSS3D || L == BOX3D) ? wrapi(iy + oy, D.ny) : 0;
             acc += lu[(long long)Off<L>::slot(i) * m + r] * vals[(long long)(lev + 1) * D.ncol + gy * D.nx + gx];
         }
-        return acc;
-    }
+    } else {
 #pragma unroll
-    for (int i0 = 0; i0 < N; i0 += CH) {
-        T a[CH], b[CH];
-        bool on[CH];
+        for (int i0 = 0; i0 < N; i0 += CH) {
+            T a[CH], b[CH];
+            bool on[CH];
 #pragma unroll
-        for (int u = 0; u < CH; ++u) {
-            const int i = i0 + u;
-            const int ox = Off<L>::ox(i), oy = Off<L>::oy(i);
-            const int nc = (cc + ox + oy) & 3;
-            on[u] = LOWER ? (nc < cc) : (nc > cc);
-            a[u] = T(0);
-            b[u] = T(0);
-            if (on[u]) {
-                const int lev = Off<L>::kk(i) < 0 ? j : w0 + Off<L>::kk(i);
-                const int gx = wrapi(ix + ox, D.nx);
-                const int gy = (L == CROSS3D || L == BOX3D) ? wrapi(iy + oy, D.ny) : 0;
-                a[u] = lu[(long long)Off<L>::slot(i) * m + r];
-                b[u] = vals[(long long)(lev + 1) * D.ncol + gy * D.nx + gx];
+            for (int u = 0; u < CH; ++u) {
+                const int i = i0 + u;
+                const int ox = Off<L>::ox(i), oy = Off<L>::oy(i);
+                const int nc = (cc + ox + oy) & 3;
+                on[u] = LOWER ? (nc < cc) : (nc > cc);
+                a[u] = T(0);
+                b[u] = T(0);
+                if (on[u]) {
+                    const int lev = Off<L>::kk(i) < 0 ? j : w0 + Off<L>::kk(i);
+                    const int gx = wrapi(ix + ox, D.nx);
+                    const int gy = (L == CROSS3D || L == BOX3D) ? wrapi(iy + oy, D.ny) : 0;
+                    a[u] = lu[(long long)Off<L>::slot(i) * m + r];
+                    b[u] = vals[(long long)(lev + 1) * D.ncol + gy * D.nx + gx];
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < CH; ++u)
-            if (on[u]) acc += a[u] * b[u];
+            for (int u = 0; u < CH; ++u)
+                if (on[u]) acc += a[u] * b[u];
+        }
     }
     return acc;
 }
