@@ -249,10 +249,21 @@ def replica_value(local_ms, nsolves_per_rank, world, dist=None, device=None):
     return world * nsolves_per_rank / (total_ms / 1e3), total_ms
 
 
-def source_hash():
+# the sources each profiled kernel is compiled from: a DRAM figure taken by
+# ncu stays valid while these files are unchanged
+KERNEL_SOURCES = {
+    "resident_kernel": ["resident.cu", "sw_solve.cuh", "sw_device.cuh", "sw_internal.cuh", "../../include/sawave.h"],
+    "solve_kernel": ["solve_kernel.cu", "solver.cu", "sw_solve.cuh", "sw_device.cuh", "sw_internal.cuh",
+                     "../../include/sawave.h"],
+}
+
+
+def source_hash(kernel=None):
+    """SHA-256 prefix of the kernel's source files (all of csrc/ when no kernel is named)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2511_18071_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    files = KERNEL_SOURCES.get(kernel) or sorted(os.listdir(d))
+    for f in files:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -272,7 +283,7 @@ def profile_traffic(kernel):
     except (OSError, ValueError):
         return None
     ent = d.get(kernel)
-    if not ent or ent.get("source_sha") != source_hash():
+    if not ent or ent.get("source_sha") != source_hash(kernel):
         return None
     return ent.get("dram_bytes_per_launch")
 
