@@ -519,18 +519,19 @@ def roofline_large(sw, torch, dev, n3d, peaks, nx2d=None):
     else:      # varying 3-D bed: 84 factor slots off the column
         off, fA, ncoef = 84, 123.0, 16
     j = 10
+    tp = ((Pl * (Pl + 1) // 2) + 3) & ~3   # packed triangle of an in-column inverse block (periodic grids)
     model = {   # bytes, flops per launch (class of launches)
         "apply": (8.0 * m + 4.0 * ncoef * ncol, fA * m, "alu"),
         "ilu_gather_fwd": (4.0 * (off / 2) * m + 8.0 * m, 2.0 * (off / 2) * m, "hbm"),
-        "ilu_products": (2.0 * 4 * Pl * Pl * ncol + 16.0 * m, 4.0 * Pl * m, "hbm"),
+        "ilu_products": (2.0 * 4 * tp * ncol + 16.0 * m, 2.0 * Pl * m, "hbm"),
         "ilu_gather_bwd": (4.0 * (off / 2) * m + 6.0 * m, 2.0 * (off / 2) * m, "hbm"),
         "cgs_pass1_j10": (4.0 * (j + 2) * m, 2.0 * (j + 1) * m, "hbm"),
         "cgs_pass2_j10": (4.0 * (j + 3) * m, 4.0 * (j + 1) * m, "hbm"),
         "cgs_pass3_j10": (4.0 * (j + 3) * m, 2.0 * (j + 1) * m + 2.0 * m, "hbm"),
     }
     # the whole application: both gathers and both block-product sweeps
-    model["ilu_application"] = (sum(model[k][0] for k in ("ilu_gather_fwd", "ilu_products", "ilu_gather_bwd")),
-                                sum(model[k][1] for k in ("ilu_gather_fwd", "ilu_products", "ilu_gather_bwd")), "hbm")
+    parts = ("ilu_gather_fwd", "ilu_products", "ilu_gather_bwd")
+    model["ilu_application"] = (sum(model[k][0] for k in parts), sum(model[k][1] for k in parts), "hbm")
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sm_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     hbm = peaks.get("hbm_gbs")
@@ -547,6 +548,7 @@ def roofline_large(sw, torch, dev, n3d, peaks, nx2d=None):
     return {"workload": name, "unknowns": m, "precision": "mixed (FP32 inner)",
             "executor": "streamed", "create_s": create_s, "solves": 2, "iters_last_solve": st["iterations"],
             "apply_form": {"column_marching": bool(col), "tile": [tx, ty]},
+            "ilu_form": "row gathers per colour, column products with packed triangular inverse blocks",
             "peaks": {"hbm_gbs": hbm, "hbm_source": "measured copy (MEASURED_PEAKS.json)",
                       "fp32_tflops": fp32_peak,
                       "fp32_source": "unit counts: %d SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % (

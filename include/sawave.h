@@ -339,7 +339,8 @@ int sw_get_phase_times(sw_problem *p, double *us, int n);
  * Arnoldi step (autotuned form), 1 the forward ILU gathers of every colour,
  * 2 the in-column block products of both sweeps, 3 the backward ILU gathers,
  * 4-6 the three Gram-Schmidt passes at Arnoldi index j = 10, 7 one whole ILU
- * application.  The control state of the last solve is restored. */
+ * application (on periodic grids the products read the packed triangular
+ * inverse blocks).  The control state of the last solve is restored. */
 int sw_profile_kernels(sw_problem *p, int reps, double *us, int n);
 /* The operator form the streamed executor's autotuner picked: *column_form 1
  * for the column-marching kernel (tile tile_x x tile_y columns), 0 for the

@@ -19,10 +19,12 @@
 #include <cstring>
 #include <mutex>
 #include <set>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
 #include "sw_colapply.cuh"
+#include "sw_ilu_packed.cuh"
 #include "sw_solve.cuh"
 
 namespace sw {
@@ -372,13 +374,118 @@ __global__ void __launch_bounds__(NTHREADS) sk_norm(const TI *v0, long long m, d
     block_partials32(v, 1, red, part, gridDim.x);
 }
 
+// Sum of two compensated FP32 partial sums (s, c): TwoSum of the leading
+// parts, both compensation terms carried (Ogita, Rump and Oishi 2005).
+__device__ __forceinline__ void ds_add(float &s, float &c, float s2, float c2) {
+    const float t = s + s2;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (s2 - bp);
+    s = t;
+    c = (c + c2) + e;
+}
+
+// Warp reduce-scatter of N compensated FP32 sums (N = 1, 2, 4, 8, 16 or 32):
+// afterwards lane l holds the warp total of value l % N in s[0] + c[0].  The
+// halving steps follow warp_reduce_scatter; the remaining lane bits are
+// summed by plain butterflies.  Only FP32 instructions: the FP64 pipe of this
+// chip issues one warp instruction per ~64 cycles per scheduler.
+template <int N>
+__device__ __forceinline__ void warp_reduce_scatter_ds(float (&s)[N], float (&c)[N], int lane) {
+#pragma unroll
+    for (int o = N / 2; o >= 1; o >>= 1) {
+        const bool upper = lane & o;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float ss = upper ? s[i] : s[i + o], cs = upper ? c[i] : c[i + o];
+            float ks = upper ? s[i + o] : s[i], kc = upper ? c[i + o] : c[i];
+            const float rs = __shfl_xor_sync(0xffffffffu, ss, o);
+            const float rc = __shfl_xor_sync(0xffffffffu, cs, o);
+            ds_add(ks, kc, rs, rc);
+            s[i] = ks;
+            c[i] = kc;
+        }
+    }
+#pragma unroll
+    for (int o = N; o < 32; o <<= 1) {
+        const float rs = __shfl_xor_sync(0xffffffffu, s[0], o);
+        const float rc = __shfl_xor_sync(0xffffffffu, c[0], o);
+        ds_add(s[0], c[0], rs, rc);
+    }
+}
+
 // CGS2 pass 1 (d_i = V_i . w), pass 2 (w -= V h; d'_i = V_i . w) and pass 3
 // (w -= V h'; ||w||^2), as in the persistent kernel: FP32 inner vectors use
 // compensated products, the coefficient sums are FP64.  NJ >= j + 1 sizes the
 // per-thread arrays, so short Arnoldi prefixes need few registers and the
 // kernel keeps more warps resident.
+//
+// FP32 vectors are read VW points at a time (16-byte loads for VW = 4, 8-byte for VW = 2): a
+// thread has NJ + 1 independent vector loads in flight per iteration.  The
+// block's partial sums are reduced across each warp in compensated FP32
+// (double-single) and only then converted to FP64, so the epilogue issues a
+// handful of FP64 instructions per warp instead of a 32-value FP64 butterfly.
+template <typename V4T, int VW> struct VecOf;
+template <> struct VecOf<float4, 4> {
+    __device__ static float get(const float4 &v, int u) { return u == 0 ? v.x : (u == 1 ? v.y : (u == 2 ? v.z : v.w)); }
+    __device__ static void set(float4 &v, int u, float a) {
+        if (u == 0) v.x = a; else if (u == 1) v.y = a; else if (u == 2) v.z = a; else v.w = a;
+    }
+    __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <> struct VecOf<float, 1> {
+    __device__ static float get(const float &v, int) { return v; }
+    __device__ static void set(float &v, int, float a) { v = a; }
+    __device__ static float zero() { return 0.f; }
+};
+template <> struct VecOf<float2, 2> {
+    __device__ static float get(const float2 &v, int u) { return u == 0 ? v.x : v.y; }
+    __device__ static void set(float2 &v, int u, float a) { if (u == 0) v.x = a; else v.y = a; }
+    __device__ static float2 zero() { return make_float2(0.f, 0.f); }
+};
+
+template <int PASS, int NJ, int VW>
+__device__ __forceinline__ void cgs_f32_body(const float *V, int j, float *w, long long m, const float *hs32,
+                                             Dot2f (&acc)[PASS == 3 ? 1 : NJ]) {
+    using VT = typename std::conditional<VW == 4, float4, typename std::conditional<VW == 2, float2, float>::type>::type;
+    using Op = VecOf<VT, VW>;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long mv = m / VW;
+    const VT *Vv = reinterpret_cast<const VT *>(V);
+    VT *wvp = reinterpret_cast<VT *>(w);
+    for (long long p = t0; p < mv; p += stride) {
+        VT vb[NJ];
+#pragma unroll
+        for (int i = 0; i < NJ; ++i) vb[i] = i <= j ? Vv[(size_t)i * mv + p] : Op::zero();
+        VT wv = wvp[p];
+        if (PASS > 1) {
+#pragma unroll
+            for (int i = 0; i < NJ; ++i) {
+                if (i > j) break;
+                const float h = -hs32[i];
+#pragma unroll
+                for (int u = 0; u < VW; ++u) Op::set(wv, u, fmaf(h, Op::get(vb[i], u), Op::get(wv, u)));
+            }
+            wvp[p] = wv;
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+            const float wu = Op::get(wv, u);
+            if (PASS == 3) {
+                acc[0].add(wu, wu);
+            } else {
+#pragma unroll
+                for (int i = 0; i < NJ; ++i) {
+                    if (i > j) break;
+                    acc[i].add(Op::get(vb[i], u), wu);
+                }
+            }
+        }
+    }
+}
+
 template <typename TI, int PASS, int NJ>
-__global__ void __launch_bounds__(NTHREADS) sk_cgs(const TI *V, int j, TI *w, long long m, const SState *ss,
+__global__ void __launch_bounds__(NTHREADS, (sizeof(TI) == 4 && NJ <= 16) ? 2 : 1) sk_cgs(const TI *V, int j, TI *w, long long m, const SState *ss,
                                                     double *part) {
     __shared__ double red[NWARPS * 32];
     __shared__ double hs[MAX_RESTART];
@@ -390,38 +497,37 @@ __global__ void __launch_bounds__(NTHREADS) sk_cgs(const TI *V, int j, TI *w, lo
     }
     __syncthreads();
     constexpr int NA = PASS == 3 ? 1 : NJ;
-    double d[NA];
-#pragma unroll
-    for (int i = 0; i < NA; ++i) d[i] = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     if constexpr (sizeof(TI) == 4) {
         Dot2f acc[NA];
-        for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += stride) {
-            float vb[NJ];
+        // the basis vectors start m points apart: with m a multiple of the
+        // vector width (always so for the library's grids, where m is a
+        // multiple of 4) every load is aligned; other m take single points
+        constexpr int VWD = NJ <= 16 ? 4 : 2;
+        if (m % VWD == 0) cgs_f32_body<PASS, NJ, VWD>((const float *)V, j, (float *)w, m, hs32, acc);
+        else cgs_f32_body<PASS, NJ, 1>((const float *)V, j, (float *)w, m, hs32, acc);
+        // block partials: compensated warp reduce-scatter, FP64 across warps
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        constexpr int NR = NA == 1 ? 1 : (NA <= 4 ? 4 : (NA <= 8 ? 8 : (NA <= 16 ? 16 : 32)));
+        float rs[NR], rc[NR];
 #pragma unroll
-            for (int i = 0; i < NJ; ++i) vb[i] = i <= j ? (float)V[(size_t)i * m + p] : 0.f;
-            float wv = (float)w[p];
-            if (PASS > 1) {
-#pragma unroll
-                for (int i = 0; i < NJ; ++i) {
-                    if (i > j) break;
-                    wv = fmaf(-hs32[i], vb[i], wv);
-                }
-                w[p] = TI(wv);
-            }
-            if (PASS == 3) {
-                acc[0].add(wv, wv);
-            } else {
-#pragma unroll
-                for (int i = 0; i < NA; ++i) {
-                    if (i > j) break;
-                    acc[i].add(vb[i], wv);
-                }
-            }
+        for (int i = 0; i < NR; ++i) {
+            rs[i] = i < NA ? acc[i < NA ? i : 0].s : 0.f;
+            rc[i] = i < NA ? acc[i < NA ? i : 0].c : 0.f;
         }
-#pragma unroll
-        for (int i = 0; i < NA; ++i) d[i] = acc[i].value();
+        warp_reduce_scatter_ds<NR>(rs, rc, lane);
+        red[warp * 32 + lane] = (double)rs[0] + (double)rc[0];
+        __syncthreads();
+        const int n = PASS == 3 ? 1 : j + 1;
+        if (warp == 0 && lane < n) {
+            double t = 0.0;
+            for (int w2 = 0; w2 < NWARPS; ++w2) t += red[w2 * 32 + lane];
+            part[lane * gridDim.x + blockIdx.x] = t;
+        }
     } else {
+        double d[NA];
+#pragma unroll
+        for (int i = 0; i < NA; ++i) d[i] = 0.0;
         for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m; p += stride) {
             double vb[NJ];
 #pragma unroll
@@ -445,20 +551,35 @@ __global__ void __launch_bounds__(NTHREADS) sk_cgs(const TI *V, int j, TI *w, lo
                 }
             }
         }
-    }
-    double v[32];
-    zero32(v);
+        double v[32];
+        zero32(v);
 #pragma unroll
-    for (int i = 0; i < NA; ++i) v[i] = d[i];
-    block_partials32(v, PASS == 3 ? 1 : j + 1, red, part, gridDim.x);
+        for (int i = 0; i < NA; ++i) v[i] = d[i];
+        block_partials32(v, PASS == 3 ? 1 : j + 1, red, part, gridDim.x);
+    }
 }
 
 template <typename TI, int PASS>
 static void launch_cgs(const TI *V, int j, TI *w, long long m, const SState *ss, double *part, cudaStream_t s) {
-    if (j < 4) sk_cgs<TI, PASS, 4><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
-    else if (j < 8) sk_cgs<TI, PASS, 8><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
-    else if (j < 16) sk_cgs<TI, PASS, 16><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
-    else sk_cgs<TI, PASS, 32><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
+    if constexpr (sizeof(TI) == 4) {
+        // FP32: per-thread arrays sized to the next multiple of four above j,
+        // so that the vector loads of a pass stay in registers
+        switch ((j + 4) / 4) {
+        case 1: sk_cgs<TI, PASS, 4><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 2: sk_cgs<TI, PASS, 8><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 3: sk_cgs<TI, PASS, 12><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 4: sk_cgs<TI, PASS, 16><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 5: sk_cgs<TI, PASS, 20><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 6: sk_cgs<TI, PASS, 24><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 7: sk_cgs<TI, PASS, 28><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        default: sk_cgs<TI, PASS, 32><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        }
+    } else {
+        if (j < 4) sk_cgs<TI, PASS, 4><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
+        else if (j < 8) sk_cgs<TI, PASS, 8><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
+        else if (j < 16) sk_cgs<TI, PASS, 16><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
+        else sk_cgs<TI, PASS, 32><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
+    }
 }
 
 // x += V y (y already carries the basis scales), FP64
@@ -755,6 +876,7 @@ struct Streamed {
     int nbA = 0;
     ColXY<float> xy32{};                         // x / y weights of the column-marching apply
     ColXY<double> xy64{};
+    void *ltri = nullptr, *utri = nullptr;       // packed inverse blocks (periodic grids)
 };
 
 template <> const ColXY<float> &xy_of<float>(const Streamed *S) { return S->xy32; }
@@ -932,6 +1054,29 @@ int setup_streamed(Problem *P) {
         }
     }
     if (e != cudaSuccess) return cuda_fail(e, "streamed executor set-up");
+    // periodic grids: packed triangles of the in-column inverse blocks (built
+    // once on the device from the dense blocks)
+    if (!D.walls) {
+        const bool f32 = P->params.precision == SW_PRECISION_MIXED;
+        const size_t es = f32 ? sizeof(float) : sizeof(double);
+        {
+            const size_t bytes = (size_t)D.ncol * tri_stride(D.P) * es;
+            void *lt = nullptr, *ut = nullptr;
+            e = cudaMalloc(&lt, bytes);
+            if (e == cudaSuccess) { P->allocs.push_back(lt); e = cudaMalloc(&ut, bytes); }
+            if (e == cudaSuccess) { P->allocs.push_back(ut); e = cudaMemset(lt, 0, bytes); }
+            if (e == cudaSuccess) e = cudaMemset(ut, 0, bytes);
+            if (e == cudaSuccess) {
+                if (f32) sk_pack_tri<float><<<4 * 152, NTHREADS>>>(D.linv32, D.uinv32, D.P, D.ncol, (float *)lt, (float *)ut);
+                else sk_pack_tri<double><<<4 * 152, NTHREADS>>>(D.linv64, D.uinv64, D.P, D.ncol, (double *)lt, (double *)ut);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "packed inverse blocks");
+            S->ltri = lt;
+            S->utri = ut;
+        }
+    }
     {
         const bool f32 = P->params.precision == SW_PRECISION_MIXED;
         if (D.walls) S->tl = f32 ? tune_tiles<float, 1>(P) : tune_tiles<double, 1>(P);
@@ -958,10 +1103,36 @@ void destroy_streamed(Problem *P) {
     P->streamed = nullptr;
 }
 
-// ILU application out = U^-1 L^-1 in (row-parallel gathers, per-column products)
+// In-column products of colour c with the packed blocks (periodic grids)
+template <typename TI>
+static void launch_product_tri(const Problem *P, int c, bool upper, TI *out, const SState *ss, int skip,
+                               cudaStream_t s) {
+    const Dev &D = P->dev;
+    const Streamed *S = (const Streamed *)P->streamed;
+    const int per = D.ncol >> 2;
+    const int pb = (per * 32 + NTHREADS - 1) / NTHREADS;
+    const TI *tri = (const TI *)(upper ? S->utri : S->ltri);
+#define SW_TRI_LAUNCH(PC)                                                                                      \
+    do {                                                                                                       \
+        if (upper) sk_ilu_product_tri<TI, false, PC, SState><<<pb, NTHREADS, 0, s>>>(D, c, tri, out, ss, skip); \
+        else sk_ilu_product_tri<TI, true, PC, SState><<<pb, NTHREADS, 0, s>>>(D, c, tri, out, ss, skip);        \
+    } while (0)
+    switch (D.P) {
+    case 10: SW_TRI_LAUNCH(10); break;
+    case 18: SW_TRI_LAUNCH(18); break;
+    case 34: SW_TRI_LAUNCH(34); break;
+    default: SW_TRI_LAUNCH(0); break;
+    }
+#undef SW_TRI_LAUNCH
+}
+
+// ILU application out = U^-1 L^-1 in (row-parallel gathers, per-column
+// products; on periodic grids the products read the packed triangles)
 template <typename TI, typename TIn, int WM>
 static void st_ilu(const Problem *P, const TIn *in, TI *out, const SState *ss, int skip, cudaStream_t s) {
     const Dev &D = P->dev;
+    // host code: D.walls here, never the device-only walls_of
+    const bool tri = !D.walls && ((const Streamed *)P->streamed)->ltri;
     const int ng = D.ngroups;
     for (int c = 0; c < ng; ++c) {
         const int per = P->goff_h[c + 1] - P->goff_h[c];
@@ -969,7 +1140,8 @@ static void st_ilu(const Problem *P, const TIn *in, TI *out, const SState *ss, i
         const int gb = (int)((rows + NTHREADS - 1) / NTHREADS);
         const int pb = (per * 32 + NTHREADS - 1) / NTHREADS;
         launch_gather<TI, TIn, true, WM>(D, c, gb, in, out, ss, skip, s);
-        sk_ilu_product<TI, WM><<<pb, NTHREADS, 0, s>>>(D, c, out, 0, ss, skip);
+        if (tri) launch_product_tri<TI>(P, c, false, out, ss, skip, s);
+        else sk_ilu_product<TI, WM><<<pb, NTHREADS, 0, s>>>(D, c, out, 0, ss, skip);
     }
     for (int c = ng - 1; c >= 0; --c) {
         const int per = P->goff_h[c + 1] - P->goff_h[c];
@@ -977,7 +1149,8 @@ static void st_ilu(const Problem *P, const TIn *in, TI *out, const SState *ss, i
         const int gb = (int)((rows + NTHREADS - 1) / NTHREADS);
         const int pb = (per * 32 + NTHREADS - 1) / NTHREADS;
         if (c < ng - 1) launch_gather<TI, TI, false, WM>(D, c, gb, out, out, ss, skip, s);
-        sk_ilu_product<TI, WM><<<pb, NTHREADS, 0, s>>>(D, c, out, 1, ss, skip);
+        if (tri) launch_product_tri<TI>(P, c, true, out, ss, skip, s);
+        else sk_ilu_product<TI, WM><<<pb, NTHREADS, 0, s>>>(D, c, out, 1, ss, skip);
     }
 }
 
@@ -1223,6 +1396,7 @@ static int profile_streamed(Problem *P, int reps, double *us, int n) {
         if (S->col) launch_col<TI>(P, V, 0, S->ss, tw, s);
         else sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, 0, S->ss, tw);
     });
+    const bool tri = !D.walls && S->ltri;
     t[1] = time_launches(s, flush, fb, reps, [&] {
         for (int c = 0; c < ng; ++c) {
             const long long rows = (long long)(P->goff_h[c + 1] - P->goff_h[c]) * D.P;
@@ -1233,7 +1407,8 @@ static int profile_streamed(Problem *P, int reps, double *us, int n) {
         for (int up = 0; up < 2; ++up)
             for (int c = 0; c < ng; ++c) {
                 const int per = P->goff_h[c + 1] - P->goff_h[c];
-                sk_ilu_product<TI, WM><<<(per * 32 + NTHREADS - 1) / NTHREADS, NTHREADS, 0, s>>>(D, c, w, up, S->ss, 0);
+                if (tri) launch_product_tri<TI>(P, c, up != 0, w, S->ss, 0, s);
+                else sk_ilu_product<TI, WM><<<(per * 32 + NTHREADS - 1) / NTHREADS, NTHREADS, 0, s>>>(D, c, w, up, S->ss, 0);
             }
     });
     t[3] = time_launches(s, flush, fb, reps, [&] {
