@@ -259,12 +259,18 @@ KERNEL_SOURCES = {
 
 
 def source_hash(kernel=None):
-    """SHA-256 prefix of the kernel's source files (all of csrc/ when no kernel is named)."""
+    """SHA-256 prefix of the kernel's source files (all of csrc/ when no kernel
+    is named), comments and blank lines left out, so that a change of wording
+    in a comment keeps a figure measured on the same code."""
+    import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2511_18071_gb300", "csrc")
     files = KERNEL_SOURCES.get(kernel) or sorted(os.listdir(d))
     for f in files:
-        h.update(open(os.path.join(d, f), "rb").read())
+        text = open(os.path.join(d, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 
