@@ -33,6 +33,26 @@ def test_every_declared_symbol_is_exported(sw):
         assert hasattr(L, n), n
 
 
+def test_host_code_never_exits_the_process(sw):
+    """nvcc compiles a host-side call to a device-only function template into
+    a process exit, without a diagnostic; such a call once ended a test run
+    with status 1 and no message.  The objects whose host code drives the
+    executors must not reference exit at all.  resident.o is left out: its
+    __noinline__ device helpers get host placeholders that reference exit and
+    that host code never calls."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    d = os.path.join(ROOT, "paper_2511_18071_gb300", "_build")
+    objs = sorted(f for f in os.listdir(d) if f.endswith(".o") and f != "resident.o")
+    assert "streamed.o" in objs and "solver.o" in objs
+    for f in objs:
+        undef = subprocess.run([nm, "-u", os.path.join(d, f)], capture_output=True, text=True, check=True).stdout
+        assert not re.search(r"\bexit\b", undef), f
+
+
 def test_bad_arguments_rejected_on_host(sw):
     h = np.ones(30)
     with pytest.raises(sw.SawaveError) as e:
