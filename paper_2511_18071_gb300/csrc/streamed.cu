@@ -559,26 +559,34 @@ __global__ void __launch_bounds__(NTHREADS, (sizeof(TI) == 4 && NJ <= 16) ? 2 : 
     }
 }
 
+// Launches one Gram-Schmidt pass and returns its number of blocks (the
+// partial sums the control kernel then reduces).  FP32: per-thread arrays
+// sized to the next multiple of four above j, so that the vector loads of a
+// pass stay in registers, and as many blocks as stay resident at once (two
+// per SM up to 16 basis vectors, one above: 128 registers or more), so a pass
+// runs in one round and its control kernel reduces few partial sums.
 template <typename TI, int PASS>
-static void launch_cgs(const TI *V, int j, TI *w, long long m, const SState *ss, double *part, cudaStream_t s) {
+static int launch_cgs(const TI *V, int j, TI *w, long long m, const SState *ss, double *part, cudaStream_t s) {
     if constexpr (sizeof(TI) == 4) {
-        // FP32: per-thread arrays sized to the next multiple of four above j,
-        // so that the vector loads of a pass stay in registers
-        switch ((j + 4) / 4) {
-        case 1: sk_cgs<TI, PASS, 4><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
-        case 2: sk_cgs<TI, PASS, 8><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
-        case 3: sk_cgs<TI, PASS, 12><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
-        case 4: sk_cgs<TI, PASS, 16><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
-        case 5: sk_cgs<TI, PASS, 20><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
-        case 6: sk_cgs<TI, PASS, 24><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
-        case 7: sk_cgs<TI, PASS, 28><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
-        default: sk_cgs<TI, PASS, 32><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        const int nj = 4 * ((j + 4) / 4);
+        const int nb = (nj <= 16 ? 2 : 1) * (SNB / 4);
+        switch (nj / 4) {
+        case 1: sk_cgs<TI, PASS, 4><<<nb, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 2: sk_cgs<TI, PASS, 8><<<nb, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 3: sk_cgs<TI, PASS, 12><<<nb, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 4: sk_cgs<TI, PASS, 16><<<nb, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 5: sk_cgs<TI, PASS, 20><<<nb, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 6: sk_cgs<TI, PASS, 24><<<nb, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        case 7: sk_cgs<TI, PASS, 28><<<nb, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
+        default: sk_cgs<TI, PASS, 32><<<nb, NTHREADS, 0, s>>>(V, j, w, m, ss, part); break;
         }
+        return nb;
     } else {
         if (j < 4) sk_cgs<TI, PASS, 4><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
         else if (j < 8) sk_cgs<TI, PASS, 8><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
         else if (j < 16) sk_cgs<TI, PASS, 16><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
         else sk_cgs<TI, PASS, 32><<<SNB, NTHREADS, 0, s>>>(V, j, w, m, ss, part);
+        return SNB;
     }
 }
 
@@ -1170,13 +1178,13 @@ static long long enqueue_cycle(const Problem *P, TI *V, TI *tw, SState *ss, doub
         if (S->col) launch_col<TI>(P, V, j, ss, tw, s);
         else sk_apply_vj<TI, WM><<<tl.ntiles, NTHREADS, smI, s>>>(D, tl, V, j, ss, tw);
         st_ilu<TI, TI, WM>(P, tw, w, ss, 1, s);
-        launch_cgs<TI, 1>(V, j, w, m, ss, partB, s);
-        sk_ctl_h<1><<<1, NTHREADS, 0, s>>>(partB, SNB, j, ss);
-        launch_cgs<TI, 2>(V, j, w, m, ss, partB, s);
-        sk_ctl_h<2><<<1, NTHREADS, 0, s>>>(partB, SNB, j, ss);
-        launch_cgs<TI, 3>(V, j, w, m, ss, partB, s);
-        sk_ctl_givens<<<1, NTHREADS, 0, s>>>(partB, SNB, j, ss, c);
-        n += 7 + 4 * D.ngroups;
+        const int nb1 = launch_cgs<TI, 1>(V, j, w, m, ss, partB, s);
+        sk_ctl_h<1><<<1, NTHREADS, 0, s>>>(partB, nb1, j, ss);
+        const int nb2 = launch_cgs<TI, 2>(V, j, w, m, ss, partB, s);
+        sk_ctl_h<2><<<1, NTHREADS, 0, s>>>(partB, nb2, j, ss);
+        const int nb3 = launch_cgs<TI, 3>(V, j, w, m, ss, partB, s);
+        sk_ctl_givens<<<1, NTHREADS, 0, s>>>(partB, nb3, j, ss, c);
+        n += 6 + 4 * D.ngroups;   // operator, 4 ngroups - 1 ILU launches, 3 passes, 3 control kernels
     }
     return n;
 }
@@ -1225,7 +1233,7 @@ static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
     st_ilu<TI, double, WM>(P, A.b, tw, ss, 0, s);
     sk_norms_b<TI><<<SNB, NTHREADS, 0, s>>>(A.b, tw, m, S->partB);
     sk_ctl_bnorm<<<1, NTHREADS, 0, s>>>(S->partB, SNB, ss, c);
-    launches += 3 + 4 * D.ngroups;
+    launches += 2 + 4 * D.ngroups;   // geometry, 4 ngroups - 1 ILU launches, norms, control
     // a7-a10: guess
     const int upd = A.pending;
     if (A.guess_mode == SW_GUESS_RRF) {
@@ -1296,7 +1304,7 @@ static int st_solve(Problem *P, const SolveArgs &A, cudaStream_t s) {
         cudaError_t e = cudaMemcpyAsync(S->h_done, &ss->done, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "streamed cycle");
-        launches += 3 + 4 * D.ngroups;
+        launches += 2 + 4 * D.ngroups;   // residual, 4 ngroups - 1 ILU launches, norm, control
         if (*S->h_done) break;
         // the Arnoldi steps of the cycle: one graph launch (the kernels of the
         // steps after the stop test return at once)
